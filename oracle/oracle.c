@@ -1,0 +1,528 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference of the LSH-MF hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load this library; the product path never does.  It
+ * shares no code, header, table or helper with the CUDA path.
+ *
+ * Each function follows one passage of the paper (arXiv 2111.11682):
+ *   oracle_signature_sums / oracle_signatures   Sec. 4.1, Eq. (3) (simLSH)
+ *   oracle_buckets                              Sec. 4.1, Alg. 1 (equal hash values)
+ *   oracle_topk_bruteforce / oracle_topk_buckets Sec. 4.1, Alg. 1 top-K search
+ *   oracle_predict_one (internal)               Sec. 3.2, Eq. (1)
+ *   oracle_rating_step                          Sec. 4.2, Eq. (5), Eq. (7)
+ *   oracle_train                                Sec. 4.2, Alg. 3 with the
+ *                                               stratified P x P block schedule
+ *   oracle_predict / oracle_rmse / oracle_loss  Eq. (1), Eq. (6), Eq. (2)
+ *
+ * Readings of passages the paper leaves open (each is also listed in the
+ * design notes):
+ *   - Phi(0) = -1, Phi(1) = +1; Upsilon maps s >= 0 to 1, so s == 0 gives 1.
+ *   - key bit g of table t is hash bit (t * bits + g).
+ *   - cnt(j, j') counts tables with equal keys; j itself is excluded; rows of
+ *     J^K are ordered by (cnt desc, j' asc); items with cnt = 0 follow in j'
+ *     order, which supplies the "random supplement" deterministically.
+ *   - R^K(i; j) = S^K(j) n R(i) with R(i) the training items of user i and
+ *     N^K(i; j) its complement in S^K(j); an empty set contributes 0 and its
+ *     parameters are not updated.
+ *   - inside term (2) the neighbour baseline uses the current b_i and the
+ *     epoch-start snapshot of bhat (bhat0); at prediction time (no updates)
+ *     the current bhat.
+ *   - the six updates of Eq. (5) are simultaneous: all right-hand sides use
+ *     the pre-step values.
+ *   - schedule: P x P blocks, user block floor(i P / M), item block
+ *     floor(j P / N); stratum s runs blocks (row (q + s) mod P, col q),
+ *     q = 0..P-1; inside a block ratings go in (j asc, i asc) order.
+ *   - learning rate of group g at epoch t (from 0): alpha_g / (1 + beta t^1.5).
+ *   - ratings are divided by rating_scale for training (Sec. 5.1); RMSE is
+ *     reported in original units; signatures use the raw integer rating.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+
+/* ------------------------------------------------------------------ */
+/* Sec. 4.1, Eq. (3): simLSH pre-sign sums and signatures               */
+/* ------------------------------------------------------------------ */
+
+static int hbit(const uint64_t *H, int32_t W, int64_t i, int64_t pos) {
+  return (int)((H[i * W + (pos >> 6)] >> (pos & 63)) & 1ULL);
+}
+
+static int64_t psi(int64_t r, int32_t pow_) {
+  int64_t v = 1;
+  for (int32_t p = 0; p < pow_; ++p) v *= r;
+  return v;
+}
+
+/* sums[(j * L + t) * bits + g] = sum over raters i of item j of
+ * Psi(r_ij) * Phi(H_i bit (t*bits+g)),  Phi(0) = -1, Phi(1) = +1. */
+int oracle_signature_sums(int64_t M, int64_t N, int32_t L, int32_t bits, int32_t psi_pow,
+                          const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
+                          const uint64_t *H, int32_t W, int64_t *sums) {
+  if (L <= 0 || bits <= 0 || bits > 32 || (int64_t)L * bits > 64LL * W) return ORC_EINVAL;
+  for (int64_t j = 0; j < N; ++j) {
+    for (int32_t t = 0; t < L; ++t) {
+      for (int32_t g = 0; g < bits; ++g) {
+        int64_t s = 0;
+        for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) {
+          int64_t i = row[p];
+          if (i < 0 || i >= M) return ORC_EINVAL;
+          int64_t phi = hbit(H, W, i, (int64_t)t * bits + g) ? 1 : -1;
+          s += psi(r[p], psi_pow) * phi;
+        }
+        sums[(j * L + t) * bits + g] = s;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+/* sig[t * N + j] = Upsilon applied bitwise: bit g set iff the sum is >= 0. */
+int oracle_signatures(int64_t M, int64_t N, int32_t L, int32_t bits, int32_t psi_pow,
+                      const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
+                      const uint64_t *H, int32_t W, uint32_t *sig) {
+  int64_t *s = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * L * bits);
+  if (!s) return ORC_ENOMEM;
+  int rc = oracle_signature_sums(M, N, L, bits, psi_pow, col_ptr, row, r, H, W, s);
+  if (rc == ORC_OK) {
+    for (int64_t j = 0; j < N; ++j)
+      for (int32_t t = 0; t < L; ++t) {
+        uint32_t key = 0;
+        for (int32_t g = 0; g < bits; ++g)
+          if (s[(j * L + t) * bits + g] >= 0) key |= 1u << g;
+        sig[(int64_t)t * N + j] = key;
+      }
+  }
+  free(s);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 1: hash tables (items grouped by equal key, per table)          */
+/* ------------------------------------------------------------------ */
+
+typedef struct { uint32_t key; int32_t j; } kj_t;
+
+static int cmp_kj(const void *a, const void *b) {
+  const kj_t *x = (const kj_t *)a, *y = (const kj_t *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+/* For each table t: items sorted by (key, j).  sorted_key/sorted_j are L x N. */
+int oracle_buckets(int64_t N, int32_t L, const uint32_t *sig, uint32_t *sorted_key, int32_t *sorted_j) {
+  kj_t *a = (kj_t *)malloc(sizeof(kj_t) * (size_t)N);
+  if (!a) return ORC_ENOMEM;
+  for (int32_t t = 0; t < L; ++t) {
+    for (int64_t j = 0; j < N; ++j) { a[j].key = sig[(int64_t)t * N + j]; a[j].j = (int32_t)j; }
+    qsort(a, (size_t)N, sizeof(kj_t), cmp_kj);
+    for (int64_t p = 0; p < N; ++p) {
+      sorted_key[(int64_t)t * N + p] = a[p].key;
+      sorted_j[(int64_t)t * N + p] = a[p].j;
+    }
+  }
+  free(a);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 1, top-K: the K most frequent co-bucketed items                 */
+/* ------------------------------------------------------------------ */
+
+/* Definition, all pairs: cnt(j, j') = #{t : sig_t(j) == sig_t(j')}; the row
+ * of j lists the first K items j' != j in (cnt desc, j' asc) order. */
+int oracle_topk_bruteforce(int64_t N, int32_t L, int32_t K, const uint32_t *sig, int32_t *nbr) {
+  if (K <= 0 || K > N - 1) return ORC_EINVAL;
+  int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  int64_t *level_n = (int64_t *)malloc(sizeof(int64_t) * (L + 2));
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!cnt || !level_n || !order) { free(cnt); free(level_n); free(order); return ORC_ENOMEM; }
+  for (int64_t j = 0; j < N; ++j) {
+    for (int64_t q = 0; q < N; ++q) {
+      int32_t c = 0;
+      for (int32_t t = 0; t < L; ++t) c += sig[(int64_t)t * N + j] == sig[(int64_t)t * N + q];
+      cnt[q] = c;
+    }
+    /* stable counting sort of j' by cnt descending (j' ascending within a level) */
+    memset(level_n, 0, sizeof(int64_t) * (L + 2));
+    for (int64_t q = 0; q < N; ++q) if (q != j) level_n[L - cnt[q] + 1]++;
+    for (int32_t c = 0; c <= L; ++c) level_n[c + 1] += level_n[c];
+    for (int64_t q = 0; q < N; ++q) if (q != j) order[level_n[L - cnt[q]]++] = (int32_t)q;
+    for (int32_t k = 0; k < K; ++k) nbr[j * K + k] = order[k];
+  }
+  free(cnt); free(level_n); free(order);
+  return ORC_OK;
+}
+
+typedef struct { int32_t cnt; int32_t j; } cand_t;
+
+static int cmp_cand(const void *a, const void *b) {
+  const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+  if (x->cnt != y->cnt) return x->cnt > y->cnt ? -1 : 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+static int64_t lower_key(const uint32_t *a, int64_t n, uint32_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) / 2; if (a[m] < key) lo = m + 1; else hi = m; }
+  return lo;
+}
+
+static int64_t upper_key(const uint32_t *a, int64_t n, uint32_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) / 2; if (a[m] <= key) lo = m + 1; else hi = m; }
+  return lo;
+}
+
+/* Same result through the hash tables: for each item, visit its bucket in
+ * each table, count collisions, rank the candidates, then fill with the
+ * smallest-index non-candidates. */
+int oracle_topk_buckets(int64_t N, int32_t L, int32_t K, const uint32_t *sig,
+                        const uint32_t *sorted_key, const int32_t *sorted_j, int32_t *nbr) {
+  if (K <= 0 || K > N - 1) return ORC_EINVAL;
+  int32_t *cnt = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+  int32_t *touched = NULL;
+  cand_t *cand = NULL;
+  int64_t cap = 0;
+  if (!cnt) return ORC_ENOMEM;
+  for (int64_t j = 0; j < N; ++j) {
+    int64_t nt = 0, total = 0;
+    for (int32_t t = 0; t < L; ++t) {
+      uint32_t key = sig[(int64_t)t * N + j];
+      const uint32_t *kt = sorted_key + (int64_t)t * N;
+      total += upper_key(kt, N, key) - lower_key(kt, N, key);
+    }
+    if (total > cap) {
+      cap = total;
+      free(touched); free(cand);
+      touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+      cand = (cand_t *)malloc(sizeof(cand_t) * (size_t)cap);
+      if (!touched || !cand) { free(cnt); free(touched); free(cand); return ORC_ENOMEM; }
+    }
+    for (int32_t t = 0; t < L; ++t) {
+      uint32_t key = sig[(int64_t)t * N + j];
+      const uint32_t *kt = sorted_key + (int64_t)t * N;
+      const int32_t *jt = sorted_j + (int64_t)t * N;
+      for (int64_t p = lower_key(kt, N, key); p < N && kt[p] == key; ++p) {
+        int32_t q = jt[p];
+        if (q == j) continue;
+        if (cnt[q]++ == 0) touched[nt++] = q;
+      }
+    }
+    for (int64_t a = 0; a < nt; ++a) { cand[a].cnt = cnt[touched[a]]; cand[a].j = touched[a]; }
+    qsort(cand, (size_t)nt, sizeof(cand_t), cmp_cand);
+    int32_t k = 0;
+    for (; k < K && k < nt; ++k) nbr[j * K + k] = cand[k].j;
+    for (int32_t q = 0; k < K && q < N; ++q)
+      if (q != j && cnt[q] == 0) nbr[j * K + k++] = q;
+    for (int64_t a = 0; a < nt; ++a) cnt[touched[a]] = 0;
+  }
+  free(cnt); free(touched); free(cand);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.2, Eq. (1): prediction; Sec. 4.2, Eq. (5): one SGD step       */
+/* ------------------------------------------------------------------ */
+
+/* Neighbour data of one rating (i, j): for k < K, expl[k] = 1 iff
+ * J^K[j][k] is in R(i), with rnb[k] its (scaled) rating and bnb[k] the
+ * bias bhat used for it in the baseline of term (2). */
+typedef struct {
+  const uint8_t *expl;
+  const double *rnb;
+  const double *bnb;
+} nb_info;
+
+/* Eq. (1).  Also returns |R^K|, |N^K| and the residuals x_k = r_ij1 - bbar_ij1. */
+static double predict_one(int32_t F, int32_t K, double mu, const double *u, const double *v, double bi,
+                          double bhj, const double *w, const double *c, nb_info nb, double *x,
+                          int32_t *nR_out, int32_t *nN_out) {
+  double bbar = mu + bi + bhj;                      /* term (1) */
+  double sumR = 0.0, sumN = 0.0;
+  int32_t nR = 0, nN = 0;
+  for (int32_t k = 0; k < K; ++k) {
+    if (nb.expl[k]) {
+      x[k] = nb.rnb[k] - (mu + bi + nb.bnb[k]);
+      sumR += x[k] * w[k];
+      nR++;
+    } else {
+      x[k] = 0.0;
+      sumN += c[k];
+      nN++;
+    }
+  }
+  double t2 = nR > 0 ? sumR / sqrt((double)nR) : 0.0;   /* term (2) */
+  double t3 = nN > 0 ? sumN / sqrt((double)nN) : 0.0;   /* term (3) */
+  double dot = 0.0;                                     /* term (4) */
+  for (int32_t f = 0; f < F; ++f) dot += u[f] * v[f];
+  *nR_out = nR;
+  *nN_out = nN;
+  return bbar + t2 + t3 + dot;
+}
+
+/* One rating: Eq. (1) then the six simultaneous updates of Eq. (5).
+ * gam/lam are ordered (b, bhat, u, v, w, c).  Returns e = r - rhat. */
+double oracle_rating_step(int32_t F, int32_t K, double r, double mu, double *u, double *v, double *bi,
+                          double *bhj, double *w, double *c, const uint8_t *expl, const double *rnb,
+                          const double *bnb, const double *gam, const double *lam) {
+  double x[1024];
+  double u0[1024];
+  nb_info nb = {expl, rnb, bnb};
+  int32_t nR, nN;
+  if (F > 1024 || K > 1024) return NAN;
+  double rhat = predict_one(F, K, mu, u, v, *bi, *bhj, w, c, nb, x, &nR, &nN);
+  double e = r - rhat;
+  double sR = nR > 0 ? 1.0 / sqrt((double)nR) : 0.0;
+  double sN = nN > 0 ? 1.0 / sqrt((double)nN) : 0.0;
+  double b_old = *bi, bh_old = *bhj;
+  *bi = b_old + gam[0] * (e - lam[0] * b_old);
+  *bhj = bh_old + gam[1] * (e - lam[1] * bh_old);
+  for (int32_t f = 0; f < F; ++f) u0[f] = u[f];
+  for (int32_t f = 0; f < F; ++f) u[f] = u0[f] + gam[2] * (e * v[f] - lam[2] * u0[f]);
+  for (int32_t f = 0; f < F; ++f) v[f] = v[f] + gam[3] * (e * u0[f] - lam[3] * v[f]);
+  for (int32_t k = 0; k < K; ++k) {
+    if (expl[k]) w[k] = w[k] + gam[4] * (sR * e * x[k] - lam[4] * w[k]);
+    else c[k] = c[k] + gam[5] * (sN * e - lam[5] * c[k]);
+  }
+  return e;
+}
+
+/* ------------------------------------------------------------------ */
+/* Training set lookups: R(i) as per-user item lists sorted by item      */
+/* ------------------------------------------------------------------ */
+
+typedef struct { int32_t j; uint8_t r; } ent_t;
+
+static int cmp_ent(const void *a, const void *b) {
+  const ent_t *x = (const ent_t *)a, *y = (const ent_t *)b;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+typedef struct { int64_t *ptr; ent_t *ent; } user_lists;
+
+static int build_user_lists(int64_t M, int64_t nnz, const int32_t *ti, const int32_t *tj,
+                            const uint8_t *tr, user_lists *ul) {
+  ul->ptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+  ul->ent = (ent_t *)malloc(sizeof(ent_t) * (size_t)(nnz > 0 ? nnz : 1));
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M + 1));
+  if (!ul->ptr || !ul->ent || !fill) { free(ul->ptr); free(ul->ent); free(fill); return ORC_ENOMEM; }
+  for (int64_t p = 0; p < nnz; ++p) ul->ptr[ti[p] + 1]++;
+  for (int64_t i = 0; i < M; ++i) ul->ptr[i + 1] += ul->ptr[i];
+  memcpy(fill, ul->ptr, sizeof(int64_t) * (size_t)(M + 1));
+  for (int64_t p = 0; p < nnz; ++p) { ent_t e = {tj[p], tr[p]}; ul->ent[fill[ti[p]]++] = e; }
+  for (int64_t i = 0; i < M; ++i)
+    qsort(ul->ent + ul->ptr[i], (size_t)(ul->ptr[i + 1] - ul->ptr[i]), sizeof(ent_t), cmp_ent);
+  free(fill);
+  return ORC_OK;
+}
+
+static void free_user_lists(user_lists *ul) { free(ul->ptr); free(ul->ent); }
+
+/* rating of item q by user i in the training set, or -1 */
+static int user_rating(const user_lists *ul, int64_t i, int32_t q) {
+  int64_t lo = ul->ptr[i], hi = ul->ptr[i + 1];
+  while (lo < hi) {
+    int64_t m = (lo + hi) / 2;
+    if (ul->ent[m].j < q) lo = m + 1; else hi = m;
+  }
+  return (lo < ul->ptr[i + 1] && ul->ent[lo].j == q) ? ul->ent[lo].r : -1;
+}
+
+static int validate(int64_t M, int64_t N, int64_t n, const int32_t *ti, const int32_t *tj) {
+  for (int64_t p = 0; p < n; ++p)
+    if (ti[p] < 0 || ti[p] >= M || tj[p] < 0 || tj[p] >= N) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+typedef struct {
+  int64_t M, N;
+  int32_t F, K, P;
+  double alpha[6];   /* b, bhat, u, v, w, c */
+  double beta;
+  double lambda[6];
+  double rating_scale;
+} oracle_cfg;
+
+/* fill expl/rnb/bnb for rating (i, j) */
+static void neighbours_of(const oracle_cfg *c, const user_lists *ul, int64_t i, int64_t j,
+                          const int32_t *nbr, const double *bh_for_nb, uint8_t *expl, double *rnb,
+                          double *bnb) {
+  for (int32_t k = 0; k < c->K; ++k) {
+    int32_t q = nbr[j * c->K + k];
+    int rv = user_rating(ul, i, q);
+    expl[k] = rv >= 0;
+    rnb[k] = rv >= 0 ? (double)rv / c->rating_scale : 0.0;
+    bnb[k] = bh_for_nb[q];
+  }
+}
+
+typedef struct { int32_t j, i; uint8_t r; } rat_t;
+
+static int cmp_rat(const void *a, const void *b) {
+  const rat_t *x = (const rat_t *)a, *y = (const rat_t *)b;
+  if (x->j != y->j) return x->j < y->j ? -1 : 1;
+  return (x->i > y->i) - (x->i < y->i);
+}
+
+/* Sec. 4.2 / Alg. 3 under the stratified schedule.  Runs strata
+ * [s_begin, s_end) of epoch `epoch` (0-based; the learning rate follows
+ * Eq. (7)).  bhat0 is taken when the call starts.  Parameters are updated in
+ * place.  *sq_err (if not NULL) receives the sum of e^2 over the processed
+ * ratings, in scaled units. */
+int oracle_train(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int32_t *tj,
+                 const uint8_t *tr, const int32_t *nbr, double mu, double *U, double *V, double *b,
+                 double *bh, double *W, double *C, int32_t epoch, int32_t s_begin, int32_t s_end,
+                 double *sq_err) {
+  const int64_t M = c->M, N = c->N, P = c->P;
+  const int32_t F = c->F, K = c->K;
+  if (P <= 0 || F <= 0 || K <= 0 || K > 1024 || F > 1024) return ORC_EINVAL;
+  if (validate(M, N, nnz, ti, tj) != ORC_OK) return ORC_EINVAL;
+  if (s_begin < 0) s_begin = 0;
+  if (s_end > P) s_end = (int32_t)P;
+
+  user_lists ul;
+  if (build_user_lists(M, nnz, ti, tj, tr, &ul) != ORC_OK) return ORC_ENOMEM;
+
+  /* ratings grouped by block (col block, row block), each block in (j, i) order */
+  int64_t nb = P * P;
+  int64_t *bptr = (int64_t *)calloc((size_t)nb + 1, sizeof(int64_t));
+  int64_t *bfill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb + 1));
+  rat_t *rat = (rat_t *)malloc(sizeof(rat_t) * (size_t)(nnz > 0 ? nnz : 1));
+  double *bh0 = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!bptr || !bfill || !rat || !bh0) {
+    free(bptr); free(bfill); free(rat); free(bh0); free_user_lists(&ul);
+    return ORC_ENOMEM;
+  }
+  for (int64_t p = 0; p < nnz; ++p) {
+    int64_t rb = ((int64_t)ti[p] * P) / M, cb = ((int64_t)tj[p] * P) / N;
+    bptr[cb * P + rb + 1]++;
+  }
+  for (int64_t k = 0; k < nb; ++k) bptr[k + 1] += bptr[k];
+  memcpy(bfill, bptr, sizeof(int64_t) * (size_t)(nb + 1));
+  for (int64_t p = 0; p < nnz; ++p) {
+    int64_t rb = ((int64_t)ti[p] * P) / M, cb = ((int64_t)tj[p] * P) / N;
+    rat_t x = {tj[p], ti[p], tr[p]};
+    rat[bfill[cb * P + rb]++] = x;
+  }
+  for (int64_t k = 0; k < nb; ++k)
+    qsort(rat + bptr[k], (size_t)(bptr[k + 1] - bptr[k]), sizeof(rat_t), cmp_rat);
+
+  memcpy(bh0, bh, sizeof(double) * (size_t)N);          /* epoch-start snapshot */
+  double gam[6], lam[6];
+  double tfac = 1.0 + c->beta * pow((double)epoch, 1.5);   /* Eq. (7) */
+  for (int g = 0; g < 6; ++g) { gam[g] = c->alpha[g] / tfac; lam[g] = c->lambda[g]; }
+
+  uint8_t expl[1024];
+  double rnb[1024], bnb[1024];
+  double se = 0.0;
+  for (int64_t s = s_begin; s < s_end; ++s) {
+    for (int64_t q = 0; q < P; ++q) {
+      int64_t rb = (q + s) % P, cb = q;
+      int64_t blk = cb * P + rb;
+      for (int64_t p = bptr[blk]; p < bptr[blk + 1]; ++p) {
+        int64_t i = rat[p].i, j = rat[p].j;
+        neighbours_of(c, &ul, i, j, nbr, bh0, expl, rnb, bnb);
+        double e = oracle_rating_step(F, K, (double)rat[p].r / c->rating_scale, mu, U + i * F, V + j * F,
+                                      b + i, bh + j, W + j * K, C + j * K, expl, rnb, bnb, gam, lam);
+        se += e * e;
+      }
+    }
+  }
+  if (sq_err) *sq_err = se;
+  free(bptr); free(bfill); free(rat); free(bh0); free_user_lists(&ul);
+  return ORC_OK;
+}
+
+/* Eq. (1) for query pairs with the current parameters (neighbour baselines
+ * use the current bhat).  R(i) is taken from the training set. */
+int oracle_predict(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int32_t *tj,
+                   const uint8_t *tr, const int32_t *nbr, double mu, const double *U, const double *V,
+                   const double *b, const double *bh, const double *W, const double *C, int64_t n,
+                   const int32_t *qi, const int32_t *qj, double *out) {
+  if (validate(c->M, c->N, nnz, ti, tj) != ORC_OK || validate(c->M, c->N, n, qi, qj) != ORC_OK)
+    return ORC_EINVAL;
+  if (c->K > 1024 || c->F > 1024) return ORC_EINVAL;
+  user_lists ul;
+  if (build_user_lists(c->M, nnz, ti, tj, tr, &ul) != ORC_OK) return ORC_ENOMEM;
+  uint8_t expl[1024];
+  double rnb[1024], bnb[1024], x[1024];
+  for (int64_t p = 0; p < n; ++p) {
+    int64_t i = qi[p], j = qj[p];
+    neighbours_of(c, &ul, i, j, nbr, bh, expl, rnb, bnb);
+    nb_info nbi = {expl, rnb, bnb};
+    int32_t nR, nN;
+    out[p] = predict_one(c->F, c->K, mu, U + i * c->F, V + j * c->F, b[i], bh[j], W + j * c->K,
+                         C + j * c->K, nbi, x, &nR, &nN);
+  }
+  free_user_lists(&ul);
+  return ORC_OK;
+}
+
+/* Eq. (6): RMSE over query pairs with ratings qr, in original units. */
+int oracle_rmse(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int32_t *tj,
+                const uint8_t *tr, const int32_t *nbr, double mu, const double *U, const double *V,
+                const double *b, const double *bh, const double *W, const double *C, int64_t n,
+                const int32_t *qi, const int32_t *qj, const uint8_t *qr, double *rmse) {
+  if (n <= 0) return ORC_EINVAL;
+  double *pr = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!pr) return ORC_ENOMEM;
+  int rc = oracle_predict(c, nnz, ti, tj, tr, nbr, mu, U, V, b, bh, W, C, n, qi, qj, pr);
+  if (rc == ORC_OK) {
+    double s = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+      double d = (double)qr[p] / c->rating_scale - pr[p];
+      s += d * d;
+    }
+    *rmse = c->rating_scale * sqrt(s / (double)n);
+  }
+  free(pr);
+  return rc;
+}
+
+/* Eq. (2): squared error over the training set plus the L2 terms
+ * (the W and C regularisers are read as sums over all entries). */
+int oracle_loss(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int32_t *tj,
+                const uint8_t *tr, const int32_t *nbr, double mu, const double *U, const double *V,
+                const double *b, const double *bh, const double *W, const double *C, double *loss) {
+  double *pr = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!pr) return ORC_ENOMEM;
+  int rc = oracle_predict(c, nnz, ti, tj, tr, nbr, mu, U, V, b, bh, W, C, nnz, ti, tj, pr);
+  if (rc == ORC_OK) {
+    double s = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) {
+      double d = (double)tr[p] / c->rating_scale - pr[p];
+      s += d * d;
+    }
+    double rb = 0, rbh = 0, ru = 0, rv = 0, rw = 0, rc2 = 0;
+    for (int64_t i = 0; i < c->M; ++i) {
+      rb += b[i] * b[i];
+      for (int32_t f = 0; f < c->F; ++f) ru += U[i * c->F + f] * U[i * c->F + f];
+    }
+    for (int64_t j = 0; j < c->N; ++j) {
+      rbh += bh[j] * bh[j];
+      for (int32_t f = 0; f < c->F; ++f) rv += V[j * c->F + f] * V[j * c->F + f];
+      for (int32_t k = 0; k < c->K; ++k) {
+        rw += W[j * c->K + k] * W[j * c->K + k];
+        rc2 += C[j * c->K + k] * C[j * c->K + k];
+      }
+    }
+    *loss = s + c->lambda[0] * rb + c->lambda[1] * rbh + c->lambda[4] * rw + c->lambda[5] * rc2 +
+            c->lambda[2] * ru + c->lambda[3] * rv;
+  }
+  free(pr);
+  return rc;
+}
+
+/* mu = mean of the (scaled) training ratings (Sec. 3.2, Alg. 3 first step). */
+double oracle_mean(int64_t nnz, const uint8_t *r, double rating_scale) {
+  double s = 0.0;
+  for (int64_t p = 0; p < nnz; ++p) s += (double)r[p];
+  return s / (double)nnz / rating_scale;
+}
