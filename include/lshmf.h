@@ -1,0 +1,179 @@
+/*
+ * lshmf.h -- C ABI of the GB300 (sm_103a) LSH-MF hot path.
+ *
+ * LSH-MF (arXiv 2111.11682) trains a nonlinear neighbourhood matrix
+ * factorisation model whose top-K item neighbours come from simLSH, a sign
+ * random projection hash of the sparse item columns.  This library runs the
+ * data-parallel path on one GPU:
+ *
+ *   lshmf_csc_from_coo      rating triples -> item-major (CSC) layout
+ *   lshmf_build_neighbours  simLSH signatures (Sec. 4.1, Eq. 3), per-table
+ *                           hash buckets and the top-K matrix J^K (Alg. 1)
+ *   lshmf_prepare_training  P x P block layout and the explicit-neighbour
+ *                           index R^K(i;j) = R(i) n S^K(j) (Sec. 4.2)
+ *   lshmf_train_epoch       one stratified SGD epoch of Eq. (1) / Eq. (5)
+ *                           with the learning rate of Eq. (7) (Alg. 3)
+ *   lshmf_predict/_rmse     Eq. (1) on query pairs, Eq. (6)
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *    pointers.  Arrays are dense, row-major, with the element types given.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that return a host value (h_*) synchronise it.
+ *  - Argument errors are detected before any launch and return LSHMF_EINVAL
+ *    (the message is available from lshmf_last_error).  Device-side errors
+ *    (bad indices found by a kernel, a bounded wait that gave up) are
+ *    recorded in the handle and returned by the next synchronising call or
+ *    by lshmf_check (LSHMF_EINVAL, LSHMF_ETIMEOUT).  CUDA failures return
+ *    LSHMF_ECUDA.  A failed call leaves outputs undefined.
+ *  - Device memory the library needs beyond the caller's arrays is owned by
+ *    the handle; a request that does not fit in free device memory returns
+ *    LSHMF_ENOMEM before anything is launched.
+ *  - One handle must not be used from two host threads at once.
+ *  - Ratings are small non-negative integers (uint8).  Signatures use the raw
+ *    integer; training uses rating / rating_scale (Sec. 5.1 divides Yahoo!
+ *    Music ratings by 20).
+ */
+#ifndef LSHMF_H
+#define LSHMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSHMF_OK = 0,
+  LSHMF_EINVAL = -1,    /* bad argument or bad input data */
+  LSHMF_ENOMEM = -2,    /* device memory admission refused the request */
+  LSHMF_ECUDA = -3,     /* a CUDA call failed */
+  LSHMF_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+  LSHMF_ESTATE = -5     /* call made in the wrong order (e.g. train before prepare) */
+} lshmf_status;
+
+typedef struct lshmf_handle lshmf_handle;
+
+/* Model and method configuration.
+ * Sec. 3.2 Table of symbols: M users (set I), N items (set J), rank F,
+ * K neighbours per item.  Sec. 4.1: L hash tables ("q" fine-grained
+ * hashings) whose keys are `bits` = p * G bits (p coarse-grained simLSH of
+ * G bits each), Psi(r) = r^psi_pow (Sec. 5.3 uses r^2 and r^4).
+ * Sec. 4.2: P strata of the P x P block schedule; learning rates alpha and
+ * regularisers lambda per parameter group in the order (b, bhat, u, v, w, c)
+ * (Eq. 5, Table "The_CUMF_LSH"); beta of Eq. (7). */
+typedef struct {
+  int64_t M, N;
+  int32_t F;            /* 1..256 */
+  int32_t K;            /* 1..64, K < N */
+  int32_t L;            /* 1..64 */
+  int32_t bits;         /* 1..32, L * bits <= 1024 */
+  int32_t psi_pow;      /* 0..4 */
+  int32_t P;            /* 1..4096 */
+  float alpha[6];
+  float beta;
+  float lambda[6];
+  float rating_scale;   /* > 0 */
+} lshmf_config;
+
+/* Model parameters, all DEVICE pointers to float32 arrays owned by the caller:
+ * U [M x F], V [N x F], b [M], bh [N] (bhat), W [N x K], C [N x K]; and the
+ * global mean mu (host value, FP64; the kernels use float(mu)). */
+typedef struct {
+  float *U, *V, *b, *bh, *W, *C;
+  double mu;
+} lshmf_params;
+
+/* Creates a handle for `cfg` on the current CUDA device.  EINVAL on a bad
+ * configuration.  *out is NULL on failure. */
+lshmf_status lshmf_create(const lshmf_config *cfg, lshmf_handle **out);
+
+/* Frees the handle and everything it owns (synchronises the device first). */
+void lshmf_destroy(lshmf_handle *h);
+
+/* Message of the last failure on this handle ("" if none); owned by the handle. */
+const char *lshmf_last_error(const lshmf_handle *h);
+
+/* Synchronises `stream` and returns the first recorded device-side error
+ * (sticky until the next prepare), or LSHMF_OK. */
+lshmf_status lshmf_check(lshmf_handle *h, void *stream);
+
+/* Number of kernels this library has launched in this process (all handles). */
+int64_t lshmf_launch_count(void);
+
+/* Item-major (CSC) layout of a rating set: Sec. 4.1 computes each item's hash
+ * from the ratings of its raters.  Input: nnz triples (d_i[p] user in [0, M),
+ * d_j[p] item in [0, N), d_r[p] rating), any order, no duplicate (i, j).
+ * Output: d_col_ptr [N + 1] int64, d_row [nnz] int32 (users ascending inside
+ * each column), d_rc [nnz] uint8.  Synchronous: returns EINVAL on an index
+ * out of range or a duplicate pair. */
+lshmf_status lshmf_csc_from_coo(lshmf_handle *h, const int32_t *d_i, const int32_t *d_j,
+                                const uint8_t *d_r, int64_t nnz, int64_t *d_col_ptr,
+                                int32_t *d_row, uint8_t *d_rc, void *stream);
+
+/* simLSH neighbour build, Sec. 4.1 and Alg. 1.
+ * For table t < L and key bit g < bits, item j's bit is Upsilon of
+ * sum over raters i of Psi(r_ij) * Phi(H_i bit (t * bits + g)) (Eq. 3), with
+ * Phi(0) = -1, Phi(1) = +1 and Upsilon(s) = [s >= 0].  Items are grouped by
+ * equal key per table; cnt(j, j') = number of tables where j and j' share a
+ * key; row j of J^K lists the K items j' != j in (cnt desc, j' asc) order
+ * (items with cnt = 0 fill the row in index order).
+ * Inputs: CSC as produced by lshmf_csc_from_coo (nnz entries); d_H [M x W]
+ * uint64 random user bits, W = ceil(L * bits / 64), bit (t*bits+g) of user i
+ * is bit ((t*bits+g) & 63) of word d_H[i * W + ((t*bits+g) >> 6)].
+ * Outputs: d_nbr [N x K] int32 (J^K); d_sig [L x N] uint32 keys, or NULL.
+ * Asynchronous. */
+lshmf_status lshmf_build_neighbours(lshmf_handle *h, const int64_t *d_col_ptr, const int32_t *d_row,
+                                    const uint8_t *d_rc, int64_t nnz, const uint64_t *d_H,
+                                    int32_t *d_nbr, uint32_t *d_sig, void *stream);
+
+/* Training layout, Sec. 4.2.  Sorts the training triples (any order, no
+ * duplicates) into the P x P blocks of the stratified schedule (user block
+ * floor(i P / M), item block floor(j P / N); inside a block (j asc, i asc)),
+ * and builds, for every rating (i, j) and k < K, whether J^K[j][k] is in
+ * R(i) (the items user i rated) together with that rating -- the sets
+ * R^K(i;j) and N^K(i;j) of Eq. (1).  d_nbr [N x K] is J^K; it is copied.
+ * *h_mu receives mu = mean(d_r) / rating_scale (FP64).  Synchronous;
+ * EINVAL on bad indices or duplicates.  Replaces any earlier layout. */
+lshmf_status lshmf_prepare_training(lshmf_handle *h, const int32_t *d_i, const int32_t *d_j,
+                                    const uint8_t *d_r, int64_t nnz, const int32_t *d_nbr,
+                                    double *h_mu, void *stream);
+
+/* One SGD epoch (Alg. 3 semantics, Sec. 4.2) over the prepared ratings.
+ * Stratum s = 0..P-1 runs blocks (user block (q + s) mod P, item block q),
+ * q = 0..P-1, concurrently; inside a block ratings go in (j asc, i asc)
+ * order.  Each rating computes rhat by Eq. (1) and applies the six updates
+ * of Eq. (5) simultaneously (right-hand sides use pre-step values) with
+ * gamma_g = alpha_g / (1 + beta * epoch^1.5) (Eq. 7, epoch counted from 0).
+ * The baseline of a neighbour inside term (2) uses the current b_i and the
+ * neighbour's bhat as it was when the epoch started.  An empty R^K or N^K
+ * contributes 0 and leaves its parameters unchanged.  The result is
+ * deterministic and independent of launch order inside a stratum.
+ * h_sq_err: if not NULL, receives sum of e^2 over the epoch (scaled units)
+ * and the call synchronises.  Requires lshmf_prepare_training. */
+lshmf_status lshmf_train_epoch(lshmf_handle *h, const lshmf_params *p, int32_t epoch,
+                               double *h_sq_err, void *stream);
+
+/* Same as lshmf_train_epoch but runs only strata [0, n_strata) (partial epoch;
+ * the bhat snapshot is taken when the call starts). */
+lshmf_status lshmf_train_strata(lshmf_handle *h, const lshmf_params *p, int32_t epoch,
+                                int32_t n_strata, double *h_sq_err, void *stream);
+
+/* Eq. (1) for n query pairs (d_users[q], d_items[q]) with the current
+ * parameters; R(i) is the prepared training set; neighbour baselines use the
+ * current bhat.  d_out [n] float32.  Asynchronous.  Requires prepare. */
+lshmf_status lshmf_predict(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users,
+                           const int32_t *d_items, int64_t n, float *d_out, void *stream);
+
+/* Eq. (6): RMSE over n held-out pairs with ratings d_r, in original rating
+ * units (rating_scale * RMSE of the scaled ratings); the sum of squares is
+ * reduced in FP64 in a fixed order (deterministic).  Synchronous. */
+lshmf_status lshmf_rmse(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users,
+                        const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,
+                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSHMF_H */

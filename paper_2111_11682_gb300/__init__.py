@@ -1,0 +1,10 @@
+"""GB300-native (sm_103a) hot path of LSH-MF (arXiv 2111.11682).
+
+The compute lives in liblshmf.so (C ABI: include/lshmf.h, CUDA sources in
+csrc/); `lshmf` is its thin Python binding over torch CUDA tensors.
+"""
+from .lshmf import (Config, LshMF, LshmfError, Params, SYMBOLS, config_from_workload, launch_count, load,
+                    library_path)
+
+__all__ = ["Config", "LshMF", "LshmfError", "Params", "SYMBOLS", "config_from_workload", "launch_count", "load",
+           "library_path"]

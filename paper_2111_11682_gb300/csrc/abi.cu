@@ -1,0 +1,164 @@
+// extern "C" entry points of liblshmf (declared in include/lshmf.h):
+// configuration and argument validation, then dispatch to the kernels.
+#include "common.cuh"
+
+namespace lshmf {
+lshmf_status csc_from_coo(Handle *h, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r, int64_t nnz,
+                          int64_t *col_ptr, int32_t *row, uint8_t *rc, cudaStream_t st);
+lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc,
+                              int64_t nnz, const uint64_t *H, int32_t *nbr, uint32_t *sig_out, cudaStream_t st);
+lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r, int64_t nnz,
+                              const int32_t *d_nbr, double *h_mu, cudaStream_t st);
+lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
+                          cudaStream_t st);
+lshmf_status predict(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, int64_t n, float *out,
+                     cudaStream_t st);
+lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, const uint8_t *qr,
+                  int64_t n, double *h_rmse, cudaStream_t st);
+
+static lshmf_status validate_config(Handle *h, const lshmf_config *c) {
+  if (!c) return set_err(h, LSHMF_EINVAL, "config is NULL");
+  if (c->M <= 0 || c->N <= 1) return set_err(h, LSHMF_EINVAL, "M must be > 0 and N > 1");
+  if (c->M >= (int64_t(1) << 31) || c->N >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "M, N < 2^31");
+  if (c->F < 1 || c->F > 256) return set_err(h, LSHMF_EINVAL, "F must be in [1, 256]");
+  if (c->K < 1 || c->K > 64) return set_err(h, LSHMF_EINVAL, "K must be in [1, 64]");
+  if (c->K >= c->N) return set_err(h, LSHMF_EINVAL, "K must be < N (K = %d, N = %lld)", c->K, (long long)c->N);
+  if (c->L < 1 || c->L > 64) return set_err(h, LSHMF_EINVAL, "L must be in [1, 64]");
+  if (c->bits < 1 || c->bits > 32) return set_err(h, LSHMF_EINVAL, "bits must be in [1, 32]");
+  if (c->L * c->bits > 1024) return set_err(h, LSHMF_EINVAL, "L * bits must be <= 1024");
+  if (c->psi_pow < 0 || c->psi_pow > 4) return set_err(h, LSHMF_EINVAL, "psi_pow must be in [0, 4]");
+  if (c->P < 1 || c->P > 4096) return set_err(h, LSHMF_EINVAL, "P must be in [1, 4096]");
+  if (!(c->rating_scale > 0.f)) return set_err(h, LSHMF_EINVAL, "rating_scale must be > 0");
+  if (!(c->beta >= 0.f)) return set_err(h, LSHMF_EINVAL, "beta must be >= 0");
+  for (int g = 0; g < 6; ++g)
+    if (!(c->alpha[g] >= 0.f) || !(c->lambda[g] >= 0.f))
+      return set_err(h, LSHMF_EINVAL, "alpha and lambda must be >= 0");
+  return LSHMF_OK;
+}
+
+}  // namespace lshmf
+
+using namespace lshmf;
+
+struct lshmf_handle {
+  Handle h;
+};
+
+static inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+lshmf_status lshmf_create(const lshmf_config *cfg, lshmf_handle **out) {
+  if (!out) return LSHMF_EINVAL;
+  *out = nullptr;
+  Handle tmp;
+  if (validate_config(&tmp, cfg) != LSHMF_OK) {
+    fprintf(stderr, "lshmf_create: %s\n", tmp.last_error.c_str());
+    return LSHMF_EINVAL;
+  }
+  lshmf_handle *hh = new (std::nothrow) lshmf_handle();
+  if (!hh) return LSHMF_ENOMEM;
+  Handle *h = &hh->h;
+  h->cfg = *cfg;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    delete hh;
+    return LSHMF_ECUDA;
+  }
+  if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMalloc(&h->d_red, 64) != cudaSuccess ||
+      cudaMemset(h->d_err, 0, 64) != cudaSuccess) {
+    cudaFree(h->d_err);
+    cudaFree(h->d_red);
+    delete hh;
+    return LSHMF_ENOMEM;
+  }
+  *out = hh;
+  return LSHMF_OK;
+}
+
+void lshmf_destroy(lshmf_handle *hh) {
+  if (!hh) return;
+  Handle *h = &hh->h;
+  cudaDeviceSynchronize();
+  for (auto &b : h->tmp) release(b);
+  for (auto &b : h->prep) release(b);
+  release(h->red_part);
+  TrainLayout &t = h->tl;
+  DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
+                    &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq};
+  for (DevBuf *b : bufs) release(*b);
+  cudaFree(h->d_err);
+  cudaFree(h->d_red);
+  delete hh;
+}
+
+const char *lshmf_last_error(const lshmf_handle *hh) { return hh ? hh->h.last_error.c_str() : "null handle"; }
+
+lshmf_status lshmf_check(lshmf_handle *hh, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  return check_device_flag(&hh->h, S(stream), "check");
+}
+
+int64_t lshmf_launch_count(void) { return g_launches.load(); }
+
+lshmf_status lshmf_csc_from_coo(lshmf_handle *hh, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r,
+                                int64_t nnz, int64_t *d_col_ptr, int32_t *d_row, uint8_t *d_rc, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "csc_from_coo: nnz out of range");
+  if (!d_col_ptr || (nnz > 0 && (!d_i || !d_j || !d_r || !d_row || !d_rc)))
+    return set_err(h, LSHMF_EINVAL, "csc_from_coo: null pointer");
+  return csc_from_coo(h, d_i, d_j, d_r, nnz, d_col_ptr, d_row, d_rc, S(stream));
+}
+
+lshmf_status lshmf_build_neighbours(lshmf_handle *hh, const int64_t *d_col_ptr, const int32_t *d_row,
+                                    const uint8_t *d_rc, int64_t nnz, const uint64_t *d_H, int32_t *d_nbr,
+                                    uint32_t *d_sig, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "build_neighbours: nnz out of range");
+  if (!d_col_ptr || !d_H || !d_nbr || (nnz > 0 && (!d_row || !d_rc)))
+    return set_err(h, LSHMF_EINVAL, "build_neighbours: null pointer");
+  return build_neighbours(h, d_col_ptr, d_row, d_rc, nnz, d_H, d_nbr, d_sig, S(stream));
+}
+
+lshmf_status lshmf_prepare_training(lshmf_handle *hh, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r,
+                                    int64_t nnz, const int32_t *d_nbr, double *h_mu, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (!d_i || !d_j || !d_r || !d_nbr) return set_err(h, LSHMF_EINVAL, "prepare_training: null pointer");
+  return prepare_training(h, d_i, d_j, d_r, nnz, d_nbr, h_mu, S(stream));
+}
+
+lshmf_status lshmf_train_epoch(lshmf_handle *hh, const lshmf_params *p, int32_t epoch, double *h_sq_err,
+                               void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  return train_strata(&hh->h, p, epoch, hh->h.cfg.P, h_sq_err, S(stream));
+}
+
+lshmf_status lshmf_train_strata(lshmf_handle *hh, const lshmf_params *p, int32_t epoch, int32_t n_strata,
+                                double *h_sq_err, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  if (n_strata < 0 || n_strata > hh->h.cfg.P)
+    return set_err(&hh->h, LSHMF_EINVAL, "train_strata: n_strata must be in [0, P]");
+  return train_strata(&hh->h, p, epoch, n_strata, h_sq_err, S(stream));
+}
+
+lshmf_status lshmf_predict(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users, const int32_t *d_items,
+                           int64_t n, float *d_out, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (n < 0) return set_err(h, LSHMF_EINVAL, "predict: n < 0");
+  if (!p || (n > 0 && (!d_users || !d_items || !d_out))) return set_err(h, LSHMF_EINVAL, "predict: null pointer");
+  return predict(h, p, d_users, d_items, n, d_out, S(stream));
+}
+
+lshmf_status lshmf_rmse(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users, const int32_t *d_items,
+                        const uint8_t *d_r, int64_t n, double *h_rmse, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (!p || !d_users || !d_items || !d_r || !h_rmse) return set_err(h, LSHMF_EINVAL, "rmse: null pointer");
+  return rmse(h, p, d_users, d_items, d_r, n, h_rmse, S(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Shared internals of liblshmf: handle state, device buffers, status and
+// launch accounting.  sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <utility>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/lshmf.h"
+
+namespace lshmf {
+
+extern std::atomic<int64_t> g_launches;
+
+// Device-side error flag values (bitwise OR of causes).
+enum : int32_t { DERR_INDEX = 1, DERR_DUP = 2, DERR_TIMEOUT = 4, DERR_CAPACITY = 8 };
+
+// Grow-only device buffer owned by a handle.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct Handle;
+lshmf_status set_err(Handle *h, lshmf_status st, const char *fmt, ...);
+lshmf_status ensure(Handle *h, DevBuf &b, size_t bytes, const char *what);
+void release(DevBuf &b);
+
+// Training layout built by lshmf_prepare_training (all in blocked order).
+struct TrainLayout {
+  bool ready = false;
+  int64_t nnz = 0;
+  int64_t nseg = 0;
+  int64_t npacked = 0;
+  int32_t max_users_per_block = 0;
+  int32_t max_segs_per_block = 0;
+  int32_t mask_words = 0;          // ceil(K / 32)
+  DevBuf sr;        // uint32 [nnz]: user slot (low 16) | rank in block (high 16)
+  DevBuf rat;       // uint8  [nnz]: rating
+  DevBuf mask;      // uint32 [nnz * mask_words]: bit k = J^K[j][k] in R(i)
+  DevBuf roff;      // int64  [nnz + 1]: offset of the rating's packed neighbour values
+  DevBuf packed;    // uint8  [npacked]: r_{i, J^K[j][k]} for the set bits, k ascending
+  DevBuf seg_j;     // int32  [nseg]: item of each (block, item) run
+  DevBuf seg_p0;    // int64  [nseg + 1]: first rating of each run
+  DevBuf blk_seg;   // int64  [P*P + 1]: first run of each block (block id = cb * P + rb)
+  DevBuf blk_user;  // int64  [P*P + 1]: first entry of each block's user table
+  DevBuf users;     // int32  [sum of users per block]: slot -> user id
+  DevBuf nbr;       // int32  [N * K]: copy of J^K
+  DevBuf user_ptr;  // int64  [M + 1]: CSR of the training set by user (items ascending)
+  DevBuf csr_j;     // int32  [nnz]
+  DevBuf csr_r;     // uint8  [nnz]
+  DevBuf bh0;       // float  [N]: bhat snapshot (per epoch)
+  DevBuf bh0n;      // float  [N * K]: bhat snapshot of each item's neighbours
+  DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
+};
+
+constexpr int PREP_BUFS = 22;
+
+struct Handle {
+  lshmf_config cfg;
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+  int32_t *d_err = nullptr;     // device error flag (sticky until prepare)
+  double *d_red = nullptr;      // small reduction output
+  DevBuf tmp[8];                // scratch: [0..5] builders, [6] radix histogram, [7] scan
+  DevBuf prep[PREP_BUFS];       // prepare_training temporaries
+  DevBuf red_part;              // per-CTA partial sums of reductions
+  TrainLayout tl;
+};
+
+inline lshmf_status cuda_status(Handle *h, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return LSHMF_OK;
+  return set_err(h, LSHMF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LSHMF_CUDA(h, call)                                              \
+  do {                                                                  \
+    cudaError_t _e = (call);                                            \
+    if (_e != cudaSuccess) return ::lshmf::cuda_status((h), _e, #call); \
+  } while (0)
+
+#define LSHMF_TRY(expr)                       \
+  do {                                        \
+    lshmf_status _s = (expr);                 \
+    if (_s != LSHMF_OK) return _s;            \
+  } while (0)
+
+// Launch wrapper: counts launches and checks the launch status.
+#define LSHMF_LAUNCH(h, kernel, grid, block, smem, stream, ...)                        \
+  do {                                                                                \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                        \
+    ::lshmf::g_launches.fetch_add(1, std::memory_order_relaxed);                       \
+    cudaError_t _e = cudaGetLastError();                                              \
+    if (_e != cudaSuccess) return ::lshmf::cuda_status((h), _e, "launch " #kernel);   \
+  } while (0)
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int bits_for(int64_t n) {  // bits needed to represent values in [0, n)
+  int b = 0;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// ---- device helpers ----
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---- sort / scan primitives (sort.cu) ----
+// Stable LSD radix sort of (key, val) pairs on key bits [0, nbits).  Results
+// end in keys_out/vals_out.  keys_in/vals_in are used as ping-pong space and
+// are clobbered.  n < 2^31.
+lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, uint64_t *keys_out,
+                              uint32_t *vals_out, int64_t n, int nbits, cudaStream_t st);
+// Exclusive scan of n int64 values (out may alias in); out[n] = total.
+lshmf_status exclusive_scan_i64(Handle *h, const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
+// Synchronously checks 0 <= x[k] < hi for k < n (EINVAL otherwise).
+lshmf_status check_range_i32(Handle *h, const int32_t *x, int64_t n, int64_t hi, cudaStream_t st, const char *what);
+// Reads the device error flag (synchronising st) and maps it to a status.
+lshmf_status check_device_flag(Handle *h, cudaStream_t st, const char *what);
+
+}  // namespace lshmf

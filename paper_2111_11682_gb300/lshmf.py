@@ -1,0 +1,237 @@
+"""Python binding of liblshmf (include/lshmf.h): argument marshalling only.
+
+Every step runs in the library's CUDA kernels; tensors are torch CUDA tensors
+(PyTorch provides device memory and streams).  There is no CPU path: if the
+library cannot be loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE"}
+
+# Every entry point declared in include/lshmf.h.
+SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
+           "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
+           "lshmf_train_strata", "lshmf_predict", "lshmf_rmse"]
+
+
+class LshmfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    """Mirror of lshmf_config.  Groups of alpha/lambda: (b, bhat, u, v, w, c)."""
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("F", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("bits", ctypes.c_int32), ("psi_pow", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("alpha", ctypes.c_float * 6), ("beta", ctypes.c_float),
+                ("lambda_", ctypes.c_float * 6), ("rating_scale", ctypes.c_float)]
+
+    @staticmethod
+    def make(M, N, F, K, L, bits, psi_pow, P, alpha, beta, lam, rating_scale=1.0):
+        c = Config()
+        c.M, c.N, c.F, c.K, c.L, c.bits, c.psi_pow, c.P = M, N, F, K, L, bits, psi_pow, P
+        for g in range(6):
+            c.alpha[g] = alpha[g]
+            c.lambda_[g] = lam[g]
+        c.beta = beta
+        c.rating_scale = rating_scale
+        return c
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("V", ctypes.c_void_p), ("b", ctypes.c_void_p), ("bh", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("C", ctypes.c_void_p), ("mu", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads liblshmf.so (building it with nvcc if asked).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"liblshmf not built: {_build.LIB} missing")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    CP = ctypes.POINTER(_CParams)
+    sig = {
+        "lshmf_create": ([ctypes.POINTER(Config), ctypes.POINTER(P)], ctypes.c_int),
+        "lshmf_destroy": ([P], None),
+        "lshmf_last_error": ([P], ctypes.c_char_p),
+        "lshmf_check": ([P, P], ctypes.c_int),
+        "lshmf_launch_count": ([], I64),
+        "lshmf_csc_from_coo": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+        "lshmf_build_neighbours": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+        "lshmf_prepare_training": ([P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_train_epoch": ([P, CP, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_train_strata": ([P, CP, I32, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_predict": ([P, CP, P, P, I64, P, P], ctypes.c_int),
+        "lshmf_rmse": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    return int(load().lshmf_launch_count())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("lshmf: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("lshmf: expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Params:
+    """Model parameters as CUDA float32 tensors plus mu (FP64 host value)."""
+    U: torch.Tensor
+    V: torch.Tensor
+    b: torch.Tensor
+    bh: torch.Tensor
+    W: torch.Tensor
+    C: torch.Tensor
+    mu: float = 0.0
+
+    @staticmethod
+    def from_init(U0, V0, K, device="cuda"):
+        U = torch.as_tensor(U0, dtype=torch.float32).to(device).contiguous()
+        V = torch.as_tensor(V0, dtype=torch.float32).to(device).contiguous()
+        M, N = U.shape[0], V.shape[0]
+        z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=device)
+        return Params(U, V, z(M), z(N), z(N, K), z(N, K))
+
+    def clone(self):
+        return Params(*(x.clone() for x in (self.U, self.V, self.b, self.bh, self.W, self.C)), mu=self.mu)
+
+    def copy_(self, other):
+        for a, b in zip((self.U, self.V, self.b, self.bh, self.W, self.C),
+                        (other.U, other.V, other.b, other.bh, other.W, other.C)):
+            a.copy_(b, non_blocking=True)
+        self.mu = other.mu
+
+    def _c(self):
+        return _CParams(*(x.data_ptr() for x in (self.U, self.V, self.b, self.bh, self.W, self.C)), self.mu)
+
+
+class LshMF:
+    """One library handle (one configuration, one prepared training set)."""
+
+    def __init__(self, cfg: Config):
+        if not torch.cuda.is_available():
+            raise RuntimeError("lshmf needs a CUDA GPU; there is no CPU implementation")
+        self.lib = load()
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = self.lib.lshmf_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise LshmfError(st, "lshmf_create failed (bad configuration?)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lshmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != OK:
+            raise LshmfError(st, self.lib.lshmf_last_error(self.h).decode())
+
+    def check(self, stream=None):
+        self._chk(self.lib.lshmf_check(self.h, _stream(stream)))
+
+    def csc_from_coo(self, i, j, r, stream=None):
+        nnz = i.numel()
+        dev = i.device
+        col_ptr = torch.empty(self.cfg.N + 1, dtype=torch.int64, device=dev)
+        row = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        rc = torch.empty(max(nnz, 1), dtype=torch.uint8, device=dev)
+        self._chk(self.lib.lshmf_csc_from_coo(self.h, _ptr(i), _ptr(j), _ptr(r), nnz, _ptr(col_ptr), _ptr(row),
+                                              _ptr(rc), _stream(stream)))
+        return col_ptr, row[:nnz], rc[:nnz]
+
+    def build_neighbours(self, col_ptr, row, rc, H, want_sig=False, nbr_out=None, stream=None):
+        """H: CUDA int64 tensor [M, W] holding the uint64 hash words."""
+        c = self.cfg
+        nbr = nbr_out if nbr_out is not None else torch.empty((c.N, c.K), dtype=torch.int32, device=row.device)
+        sig = torch.empty((c.L, c.N), dtype=torch.int32, device=row.device) if want_sig else None
+        self._chk(self.lib.lshmf_build_neighbours(self.h, _ptr(col_ptr), _ptr(row), _ptr(rc), row.numel(), _ptr(H),
+                                                  _ptr(nbr), _ptr(sig), _stream(stream)))
+        return (nbr, sig) if want_sig else nbr
+
+    def prepare_training(self, i, j, r, nbr, stream=None) -> float:
+        mu = ctypes.c_double(0.0)
+        self._chk(self.lib.lshmf_prepare_training(self.h, _ptr(i), _ptr(j), _ptr(r), i.numel(), _ptr(nbr),
+                                                  ctypes.byref(mu), _stream(stream)))
+        return mu.value
+
+    def train_epoch(self, p: Params, epoch: int, want_sq_err=False, stream=None):
+        cp = p._c()
+        se = ctypes.c_double(0.0)
+        self._chk(self.lib.lshmf_train_epoch(self.h, ctypes.byref(cp), epoch,
+                                             ctypes.byref(se) if want_sq_err else None, _stream(stream)))
+        return se.value if want_sq_err else None
+
+    def train_strata(self, p: Params, epoch: int, n_strata: int, want_sq_err=False, stream=None):
+        cp = p._c()
+        se = ctypes.c_double(0.0)
+        self._chk(self.lib.lshmf_train_strata(self.h, ctypes.byref(cp), epoch, n_strata,
+                                              ctypes.byref(se) if want_sq_err else None, _stream(stream)))
+        return se.value if want_sq_err else None
+
+    def predict(self, p: Params, users, items, stream=None):
+        out = torch.empty(users.numel(), dtype=torch.float32, device=users.device)
+        cp = p._c()
+        self._chk(self.lib.lshmf_predict(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), users.numel(), _ptr(out),
+                                         _stream(stream)))
+        return out
+
+    def rmse(self, p: Params, users, items, r, stream=None) -> float:
+        cp = p._c()
+        out = ctypes.c_double(0.0)
+        self._chk(self.lib.lshmf_rmse(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), _ptr(r), users.numel(),
+                                      ctypes.byref(out), _stream(stream)))
+        return out.value
+
+
+def config_from_workload(w, P=None) -> Config:
+    """Config from a workload description (any object with the Workload fields)."""
+    return Config.make(w.M, w.N, w.F, w.K, w.L, w.bits, w.psi_pow, P if P is not None else w.P, w.alpha, w.beta,
+                       w.lam, w.rating_scale)
