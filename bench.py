@@ -1,0 +1,338 @@
+"""Benchmark of the LSH-MF hot path on GB300.
+
+A step is one whole training job on the Netflix-shaped workload
+(480k users x 17,770 items, 100M ratings, F = K = 64, L = 16 tables x 12 bits,
+10 epochs): COO -> CSC, simLSH neighbour build (signatures, buckets, top-K),
+training layout with the explicit-neighbour index, 10 stratified SGD epochs,
+held-out RMSE.  `value` = rating-updates/s = epochs * nnz_train / step time,
+inputs resident in HBM.  `e2e` = the same with the inputs copied from pinned
+host memory inside every timed step and the RMSE read back.
+
+--impl reference times the FP64 CPU oracle (the only reference there is: the
+paper ships no code) on a bounded sample of the same workload.
+Multi-GPU: replicas only (one independent job per rank), weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid")
+    ap.add_argument("--P", type=int, default=0, help="strata (0 = workload default)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile(src_hash):
+    """Per-launch DRAM bytes of the SGD kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "sgd_stratum_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha1") == src_hash:
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    for fn in ("train.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2111_11682_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sgd_bytes_per_epoch(stats, w):
+    """Algorithmic bytes of one epoch in the paper's memory model (Sec. 4.2, Alg. 3:
+    item parameters stay on chip, u_i and b_i are read and written per rating):
+    per rating 4 (user slot) + 1 (rating) + K/8 (mask) + 8F (u_i r/w) + 8 (b_i r/w),
+    plus one byte per explicit neighbour rating."""
+    nnz = stats["nnz"]
+    return nnz * (4 + 1 + w.K / 8 + 8 * w.F + 8) + stats["explicit_neighbours"]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import synth
+    from paper_2111_11682_gb300 import LshMF, Params, config_from_workload, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.WORKLOADS[args.workload]
+    P = args.P or w.P
+    t0 = time.time()
+    d = synth.generate(w)
+    gen_s = time.time() - t0
+    E = w.epochs
+    nnz = len(d["train_i"])
+    host = {k: torch.from_numpy(np.ascontiguousarray(d[k])).pin_memory()
+            for k in ("train_i", "train_j", "train_r", "test_i", "test_j", "test_r", "U0", "V0")}
+    host["H"] = torch.from_numpy(np.ascontiguousarray(d["H"]).view(np.int64)).pin_memory()
+    dv = {k: v.to(dev) for k, v in host.items()}
+    m = LshMF(config_from_workload(w, P))
+    init = Params.from_init(dv["U0"], dv["V0"], w.K, dev)
+    p = init.clone()
+    stream = torch.cuda.current_stream()
+    epoch_events = []
+
+    def job(src, record_epochs):
+        p.copy_(init) if src is dv else None
+        col_ptr, row, rc = m.csc_from_coo(src["train_i"], src["train_j"], src["train_r"])
+        nbr = m.build_neighbours(col_ptr, row, rc, src["H"])
+        p.mu = m.prepare_training(src["train_i"], src["train_j"], src["train_r"], nbr)
+        for e in range(E):
+            if record_epochs:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                m.train_epoch(p, e)
+                b.record(stream)
+                epoch_events.append((a, b))
+            else:
+                m.train_epoch(p, e)
+        return m.rmse(p, src["test_i"], src["test_j"], src["test_r"])
+
+    def job_e2e():
+        src = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        p.U.copy_(src["U0"], non_blocking=True)
+        p.V.copy_(src["V0"], non_blocking=True)
+        for x in (p.b, p.bh, p.W, p.C):
+            x.zero_()
+        return job(src, False)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        rmse = job(dv, False)
+    stats = m.training_stats()
+    clk = Clocks(local_rank)
+    barrier()
+    clk.start()
+    l0 = launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rmse = job(dv, True)
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    launches = launch_count() - l0
+    ms_total = ev0.elapsed_time(ev1)
+    epoch_ms = [a.elapsed_time(b) for a, b in epoch_events]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * E * nnz / (ms_step / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        job_e2e()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            rmse_e2e = job_e2e()
+        e1.record(stream)
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        e2e = {"value": world * E * nnz / (ms_e2e / 1e3), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+
+    peak, peak_kind = peaks()
+    ep_med = float(np.median(epoch_ms))
+    bytes_ep = sgd_bytes_per_epoch(stats, w)
+    achieved = bytes_ep / (ep_med / 1e3) / 1e9
+    prof = traffic_from_profile(kernel_hash())
+    traffic = None
+    if prof is not None:
+        traffic = prof["dram_bytes_per_launch"]
+    roof = {"bound": "hbm", "kernel": "k_sgd_stratum (one epoch = P launches)", "achieved": round(achieved, 1),
+            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "algorithmic_bytes_per_epoch": int(bytes_ep), "launches_per_epoch": P,
+            "epoch_ms_median": round(ep_med, 3), "note": f"frac of {peak_kind} HBM copy bandwidth"}
+
+    out = {"metric": "SGD rating-updates/s per epoch at RMSE parity (whole training job)", "value": value,
+           "unit": "rating-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (SGD), int32/int64 (simLSH)", "data": "synthetic (seeded generator, Netflix-shaped)",
+           "config": {"workload": w.name, "M": w.M, "N": w.N, "nnz_train": nnz, "F": w.F, "K": w.K, "L": w.L,
+                      "bits": w.bits, "psi_pow": w.psi_pow, "epochs": E, "P": P,
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
+           "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+           "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
+           "generate_s": round(gen_s, 1)}
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, sample_frac):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the same shape (N, F, K, L, bits, epochs) with users and ratings
+    scaled by `sample_frac`; the whole job (signatures, top-K, all epochs)."""
+    import oracle
+    import synth
+    ws = synth.scaled(w, sample_frac)
+    d = synth.generate(ws)
+    t0 = time.time()
+    col_ptr, row, r = oracle.csc(ws.M, ws.N, d["train_i"], d["train_j"], d["train_r"])
+    sig = oracle.signatures(ws.M, ws.N, ws.L, ws.bits, ws.psi_pow, col_ptr, row, r, d["H"])
+    nbr = oracle.topk_buckets(sig, ws.K)
+    t_nb = time.time() - t0
+    cfg = oracle.cfg_from_workload(ws)
+    mu = oracle.mean(d["train_r"], ws.rating_scale)
+    po = oracle.Params.init(d["U0"], d["V0"], ws.K)
+    t1 = time.time()
+    for e in range(ws.epochs):
+        oracle.train(cfg, d["train_i"], d["train_j"], d["train_r"], nbr, mu, po, e)
+    t_ep = (time.time() - t1) / ws.epochs
+    rm = oracle.rmse(cfg, d["train_i"], d["train_j"], d["train_r"], nbr, mu, po, d["test_i"], d["test_j"], d["test_r"])
+    total = time.time() - t0
+    nnz = len(d["train_i"])
+    return {"value": ws.epochs * nnz / total, "unit": "rating-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{ws.name}: {ws.M} users x {ws.N} items, {nnz} training ratings, whole job "
+                      f"({ws.epochs} epochs) in {total:.1f} s",
+            "epoch_rating_updates_per_s": nnz / t_ep, "neighbour_build_s": round(t_nb, 2), "rmse_heldout": rm}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    res = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, 0.002)
+    t0 = time.time()
+    for _ in range(args.steps):
+        res.append(cpu_baseline(w, 0.002))
+    total = time.time() - t0
+    v = float(np.mean([r["value"] for r in res]))
+    cb = dict(res[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": "SGD rating-updates/s per epoch at RMSE parity (whole training job)",
+           "value": v, "unit": "rating-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, Netflix-shaped)",
+           "config": {"workload": w.name, "sample": cb["sample"]}, "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "rating-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,23 @@ lshmf_status lshmf_train_epoch(lshmf_handle *h, const lshmf_params *p, int32_t e
 lshmf_status lshmf_train_strata(lshmf_handle *h, const lshmf_params *p, int32_t epoch,
                                 int32_t n_strata, double *h_sq_err, void *stream);
 
+/* Sizes of the prepared training layout (for memory planning and for the
+ * algorithmic byte count of an epoch: every rating reads its user slot,
+ * rating and K-bit mask, the ratings of its explicit neighbours (Sec. 4.2:
+ * R^K(i;j) = R(i) n S^K(j)), and reads and writes u_i and b_i). */
+typedef struct {
+  int64_t nnz;                      /* training ratings */
+  int64_t segments;                 /* (block, item) runs */
+  int64_t explicit_neighbours;      /* sum over ratings of |R^K(i;j)| */
+  int64_t blocks;                   /* P * P */
+  int32_t max_users_per_block;
+  int32_t max_segments_per_block;
+  int64_t device_bytes;             /* device memory held by the handle */
+} lshmf_train_stats;
+
+/* Fills *out from the last successful lshmf_prepare_training (ESTATE before). */
+lshmf_status lshmf_training_stats(const lshmf_handle *h, lshmf_train_stats *out);
+
 /* Eq. (1) for n query pairs (d_users[q], d_items[q]) with the current
  * parameters; R(i) is the prepared training set; neighbour baselines use the
  * current bhat.  d_out [n] float32.  Asynchronous.  Requires prepare. */

@@ -144,6 +144,27 @@ lshmf_status lshmf_train_strata(lshmf_handle *hh, const lshmf_params *p, int32_t
   return train_strata(&hh->h, p, epoch, n_strata, h_sq_err, S(stream));
 }
 
+lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out) {
+  if (!hh || !out) return LSHMF_EINVAL;
+  const Handle *h = &hh->h;
+  const TrainLayout &t = h->tl;
+  if (!t.ready) return LSHMF_ESTATE;
+  out->nnz = t.nnz;
+  out->segments = t.nseg;
+  out->explicit_neighbours = t.npacked;
+  out->blocks = int64_t(h->cfg.P) * h->cfg.P;
+  out->max_users_per_block = t.max_users_per_block;
+  out->max_segments_per_block = t.max_segs_per_block;
+  int64_t bytes = 0;
+  for (const auto &b : h->tmp) bytes += b.bytes;
+  for (const auto &b : h->prep) bytes += b.bytes;
+  const DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
+                          &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq};
+  for (const DevBuf *b : bufs) bytes += b->bytes;
+  out->device_bytes = bytes + h->red_part.bytes;
+  return LSHMF_OK;
+}
+
 lshmf_status lshmf_predict(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users, const int32_t *d_items,
                            int64_t n, float *d_out, void *stream) {
   if (!hh) return LSHMF_EINVAL;

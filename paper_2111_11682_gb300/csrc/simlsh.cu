@@ -259,11 +259,10 @@ static lshmf_status dispatch_sig(Handle *h, int W, const int64_t *col_ptr, const
     case 2: return run_signatures<2, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
     case 3: return run_signatures<3, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
     case 4: return run_signatures<4, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 5: case 6: case 7: case 8: return set_err(h, LSHMF_EINVAL, "internal: W not padded");
-    default: break;
+    case 8: return run_signatures<8, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
+    case 16: return run_signatures<16, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
+    default: return set_err(h, LSHMF_EINVAL, "internal: unsupported padded word count %d", W);
   }
-  if (W <= 8) return run_signatures<8, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-  return run_signatures<16, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
 }
 
 // ------------------------------------------------------------ buckets ----

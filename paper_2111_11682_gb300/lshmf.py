@@ -20,7 +20,7 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 # Every entry point declared in include/lshmf.h.
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
-           "lshmf_train_strata", "lshmf_predict", "lshmf_rmse"]
+           "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse"]
 
 
 class LshmfError(RuntimeError):
@@ -46,6 +46,15 @@ class Config(ctypes.Structure):
         c.beta = beta
         c.rating_scale = rating_scale
         return c
+
+
+class TrainStats(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("segments", ctypes.c_int64), ("explicit_neighbours", ctypes.c_int64),
+                ("blocks", ctypes.c_int64), ("max_users_per_block", ctypes.c_int32),
+                ("max_segments_per_block", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class _CParams(ctypes.Structure):
@@ -83,6 +92,7 @@ def load(build_if_missing: bool = True):
         "lshmf_prepare_training": ([P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_train_epoch": ([P, CP, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_train_strata": ([P, CP, I32, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_training_stats": ([P, ctypes.POINTER(TrainStats)], ctypes.c_int),
         "lshmf_predict": ([P, CP, P, P, I64, P, P], ctypes.c_int),
         "lshmf_rmse": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
     }
@@ -215,6 +225,11 @@ class LshMF:
         self._chk(self.lib.lshmf_train_strata(self.h, ctypes.byref(cp), epoch, n_strata,
                                               ctypes.byref(se) if want_sq_err else None, _stream(stream)))
         return se.value if want_sq_err else None
+
+    def training_stats(self) -> dict:
+        st = TrainStats()
+        self._chk(self.lib.lshmf_training_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
 
     def predict(self, p: Params, users, items, stream=None):
         out = torch.empty(users.numel(), dtype=torch.float32, device=users.device)
