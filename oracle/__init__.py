@@ -55,6 +55,7 @@ def _load():
         "oracle_buckets": [I64, I32, P, P, P],
         "oracle_topk_bruteforce": [I64, I32, I32, P, P],
         "oracle_topk_buckets": [I64, I32, I32, P, P, P, P],
+        "oracle_topk_rows": [I64, I32, I32, P, I64, P, P],
         "oracle_rating_step": [I32, I32, D, D, P, P, P, P, P, P, P, P, P, P, P],
         "oracle_train": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I32, I32, I32, P],
         "oracle_predict": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P],
@@ -130,6 +131,16 @@ def topk_bruteforce(sig, K):
     L, N = sig.shape
     out = np.zeros((N, K), dtype=np.int32)
     _check(_load().oracle_topk_bruteforce(N, L, K, _p(sig), _p(out)), "topk_bruteforce")
+    return out
+
+
+def topk_rows(sig, K, rows):
+    """Rows of J^K for the given items by the all-pairs definition (any N)."""
+    sig = _c(sig, np.uint32)
+    L, N = sig.shape
+    rows = _c(rows, np.int32)
+    out = np.zeros((len(rows), K), dtype=np.int32)
+    _check(_load().oracle_topk_rows(N, L, K, _p(sig), len(rows), _p(rows), _p(out)), "topk_rows")
     return out
 
 

@@ -160,6 +160,33 @@ int oracle_topk_bruteforce(int64_t N, int32_t L, int32_t K, const uint32_t *sig,
   return ORC_OK;
 }
 
+/* The same definition for selected items only (rows[r] = item), for large N
+ * where all pairs are out of reach: out is nrows x K. */
+int oracle_topk_rows(int64_t N, int32_t L, int32_t K, const uint32_t *sig, int64_t nrows, const int32_t *rows,
+                     int32_t *out) {
+  if (K <= 0 || K > N - 1) return ORC_EINVAL;
+  int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  int64_t *level_n = (int64_t *)malloc(sizeof(int64_t) * (L + 2));
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!cnt || !level_n || !order) { free(cnt); free(level_n); free(order); return ORC_ENOMEM; }
+  for (int64_t x = 0; x < nrows; ++x) {
+    const int64_t j = rows[x];
+    if (j < 0 || j >= N) { free(cnt); free(level_n); free(order); return ORC_EINVAL; }
+    for (int64_t q = 0; q < N; ++q) {
+      int32_t c = 0;
+      for (int32_t t = 0; t < L; ++t) c += sig[(int64_t)t * N + j] == sig[(int64_t)t * N + q];
+      cnt[q] = c;
+    }
+    memset(level_n, 0, sizeof(int64_t) * (L + 2));
+    for (int64_t q = 0; q < N; ++q) if (q != j) level_n[L - cnt[q] + 1]++;
+    for (int32_t c = 0; c <= L; ++c) level_n[c + 1] += level_n[c];
+    for (int64_t q = 0; q < N; ++q) if (q != j) order[level_n[L - cnt[q]]++] = (int32_t)q;
+    for (int32_t k = 0; k < K; ++k) out[x * K + k] = order[k];
+  }
+  free(cnt); free(level_n); free(order);
+  return ORC_OK;
+}
+
 typedef struct { int32_t cnt; int32_t j; } cand_t;
 
 static int cmp_cand(const void *a, const void *b) {

@@ -83,6 +83,7 @@ void lshmf_destroy(lshmf_handle *hh) {
   for (auto &b : h->tmp) release(b);
   for (auto &b : h->prep) release(b);
   release(h->red_part);
+  release(h->aux);
   TrainLayout &t = h->tl;
   DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                     &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq};

@@ -75,6 +75,7 @@ struct Handle {
   DevBuf tmp[8];                // scratch: [0..5] builders, [6] radix histogram, [7] scan
   DevBuf prep[PREP_BUFS];       // prepare_training temporaries
   DevBuf red_part;              // per-CTA partial sums of reductions
+  DevBuf aux;                   // top-K overflow tables
   TrainLayout tl;
 };
 

@@ -7,11 +7,16 @@
 //       or a 4096-rating chunk of a heavy one); lane l owns hash bits l, l+32,
 //       ... of every word, so one broadcast load of H_i's words feeds all
 //       lanes; Psi * bit is accumulated exactly in int32 or int64.
-//   radix sort of (t, key) -> item         per-table buckets
-//   k_topk                                 per item: visit its bucket in each
-//       table, count collisions in a warp-private open-addressing table,
-//       bitonic-sort candidates by (cnt desc, item asc), fill short rows with
-//       the smallest non-candidate items.
+//   classes of identical keys              items whose L keys all agree have
+//       equal collision counts with everyone; they are grouped (hash sort with
+//       an exact equality check) so top-K work is per class, not per item.
+//   radix sort of (t, key) -> class        per-table buckets of classes
+//   k_topk_classes                         per class: count shared buckets with
+//       other classes in a warp-private open-addressing table, rank items of
+//       other classes by (count desc, item asc) with a k-way merge of the
+//       classes' member lists, fill with the smallest non-candidate items;
+//   k_write_rows                           row of item j = its own class (all
+//       L tables shared) in index order, then the class ranking.
 #include <algorithm>
 
 #include "common.cuh"
@@ -265,47 +270,106 @@ static lshmf_status dispatch_sig(Handle *h, int W, const int64_t *col_ptr, const
   }
 }
 
-// ------------------------------------------------------------ buckets ----
-__global__ void k_bucket_keys(const uint32_t *sig, int64_t N, int L, int bits, uint64_t *keys, uint32_t *vals) {
-  const int64_t n = int64_t(L) * N;
-  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n;
-       x += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t t = x / N, j = x - t * N;
-    keys[x] = (uint64_t(t) << bits) | sig[x];
-    vals[x] = uint32_t(j);
+// ------------------------------------------------- identical-key classes ----
+// Items whose L keys are all equal have the same collision count with every
+// other item (Alg. 1 counts per table), so they are grouped into classes; the
+// candidate search then runs once per class and over classes, which bounds the
+// work on degenerate inputs (every item without raters has the all-ones key).
+// A class is found by sorting a 64-bit hash of the L keys; equal hashes with
+// different keys are detected and the hash is redrawn, so grouping is exact.
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 33)) * 0xff51afd7ed558ccdull;
+  z = (z ^ (z >> 33)) * 0xc4ceb9fe1a85ec53ull;
+  return z ^ (z >> 33);
+}
+
+__global__ void k_sig_hash(const uint32_t *sig, int64_t N, int L, uint64_t seed, uint64_t *keys, uint32_t *vals) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < N; j += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t hsh = seed;
+    for (int t = 0; t < L; ++t) hsh = mix64(hsh ^ (uint64_t(sig[int64_t(t) * N + j]) | (uint64_t(t) << 32)));
+    keys[j] = hsh;
+    vals[j] = uint32_t(j);
+  }
+}
+
+constexpr int32_t DERR_HASH = 16;
+
+__global__ void k_class_flags(const uint64_t *hs, const uint32_t *js, const uint32_t *sig, int64_t N, int L,
+                              int64_t *flag, int32_t *err) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < N; x += int64_t(gridDim.x) * blockDim.x) {
+    const bool start = x == 0 || hs[x] != hs[x - 1];
+    flag[x] = start ? 1 : 0;
+    if (!start) {
+      const int64_t a = js[x], b = js[x - 1];
+      for (int t = 0; t < L; ++t)
+        if (sig[int64_t(t) * N + a] != sig[int64_t(t) * N + b]) {
+          atomicOr(err, DERR_HASH);
+          break;
+        }
+    }
+  }
+}
+
+__global__ void k_class_emit(const int64_t *flag, const int64_t *scan, const uint32_t *js, int64_t N,
+                             int32_t *class_of, int32_t *pos_of, int64_t *class_start) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < N; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t cls = scan[x] - (flag[x] ? 0 : 1);
+    class_of[js[x]] = int32_t(cls);
+    pos_of[js[x]] = int32_t(x);
+    if (flag[x]) class_start[cls] = x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) class_start[scan[N]] = N;
+}
+
+__global__ void k_class_bucket_keys(const uint32_t *sig, const uint32_t *members, const int64_t *cs, int64_t N,
+                                    int64_t ncls, int L, int bits, uint64_t *keys, uint32_t *vals) {
+  const int64_t n = int64_t(L) * ncls;
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t t = x / ncls, c = x - t * ncls;
+    const int64_t rep = members[cs[c]];
+    keys[x] = (uint64_t(t) << bits) | sig[t * N + rep];
+    vals[x] = uint32_t(c);
   }
 }
 
 // --------------------------------------------------------------- top-K ----
 constexpr int TK_WARPS = 4;
-constexpr int TK_HC = 1024;     // warp-private hash capacity (entries)
+constexpr int TK_LOGC = 10;           // warp-private table: 1024 classes
+constexpr int TK_HC = 1 << TK_LOGC;
 
-struct TopkSmem {
+struct TopkWarp {                     // shared-memory state of one warp
   int32_t keys[TK_HC];
   int32_t cnts[TK_HC];
-  uint64_t list[TK_HC];
-  int64_t lo[64];
-  int64_t hi[64];
+  int32_t cid[TK_HC / 2];
+  int32_t ccnt[TK_HC / 2];
+  int32_t head[TK_HC / 2];
+  int32_t end[TK_HC / 2];
+  int32_t lo[64];
+  int32_t hi[64];
 };
 
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t n, uint64_t key) {
-  int64_t lo = 0, hi = n;
+struct TopkView {                     // the same state anywhere (shared or global)
+  int32_t *keys, *cnts, *cid, *ccnt, *head, *end, *lo, *hi;
+  int logc;
+};
+
+__device__ __forceinline__ int32_t lower_bound_u64(const uint64_t *a, int32_t n, uint64_t key) {
+  int32_t lo = 0, hi = n;
   while (lo < hi) {
-    int64_t m = (lo + hi) >> 1;
+    const int32_t m = (lo + hi) >> 1;
     if (a[m] < key) lo = m + 1; else hi = m;
   }
   return lo;
 }
 
-__device__ __forceinline__ uint32_t hslot(int32_t q, int logc) {
-  return (uint32_t(q) * 2654435761u) >> (32 - logc);
-}
+__device__ __forceinline__ uint32_t hslot(int32_t q, int logc) { return (uint32_t(q) * 2654435761u) >> (32 - logc); }
 
 __device__ __forceinline__ void h_insert(int32_t *keys, int32_t *cnts, int logc, int32_t q) {
   uint32_t s = hslot(q, logc);
   const uint32_t m = (1u << logc) - 1;
   while (true) {
-    int32_t old = atomicCAS(&keys[s], -1, q);
+    const int32_t old = atomicCAS(&keys[s], -1, q);
     if (old == -1 || old == q) {
       atomicAdd(&cnts[s], 1);
       return;
@@ -318,133 +382,188 @@ __device__ __forceinline__ bool h_contains(const int32_t *keys, int logc, int32_
   uint32_t s = hslot(q, logc);
   const uint32_t m = (1u << logc) - 1;
   while (true) {
-    int32_t k = keys[s];
+    const int32_t k = keys[s];
     if (k == q) return true;
     if (k == -1) return false;
     s = (s + 1) & m;
   }
 }
 
-// Top-K of one item with a warp-private table of capacity 2^logc
-// (keys/cnts) and a sort list of the same capacity.
-__device__ void topk_item(int64_t j, const uint32_t *sig, const uint64_t *skeys, const uint32_t *sj,
-                          int64_t N, int L, int bits, int K, int32_t *keys, int32_t *cnts, uint64_t *list,
-                          const int64_t *lo, const int64_t *hi, int logc, int32_t *nbr) {
+struct ClassArgs {
+  const uint32_t *sig;
+  const uint64_t *skeys;   // [L x ncls] (t, key) sorted
+  const uint32_t *scls;    // [L x ncls] class of each sorted entry
+  const uint32_t *members; // [N] items grouped by class, ascending inside a class
+  const int64_t *cs;       // [ncls + 1] class starts
+  const int32_t *class_of; // [N]
+  int64_t N, ncls;
+  int L, bits, K;
+  int32_t *rest;           // [ncls x K] ranked items from other classes
+};
+
+// Candidate count bound of class A: sum over tables of its bucket size minus itself.
+__device__ int32_t class_bucket_ranges(const ClassArgs &a, int64_t A, int32_t *lo, int32_t *hi) {
   const int lane = threadIdx.x & 31;
-  const int cap = 1 << logc;
+  const int64_t rep = a.members[a.cs[A]];
+  int32_t tot = 0;
+  for (int t = lane; t < a.L; t += 32) {
+    const uint64_t key = (uint64_t(t) << a.bits) | a.sig[int64_t(t) * a.N + rep];
+    const uint64_t *kt = a.skeys + int64_t(t) * a.ncls;
+    lo[t] = lower_bound_u64(kt, int32_t(a.ncls), key);
+    hi[t] = lower_bound_u64(kt, int32_t(a.ncls), key + 1);
+    tot += hi[t] - lo[t] - 1;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  __syncwarp();
+  return tot;
+}
+
+// Ranks the items of other classes for class A: classes sharing a key in c
+// tables (c < L) in descending c, items ascending inside a level (k-way merge
+// of the classes' member lists), then items of no candidate class by index.
+__device__ void class_rank(const ClassArgs &a, int64_t A, int need, const TopkView &v) {
+  const int lane = threadIdx.x & 31;
+  const int cap = 1 << v.logc;
   for (int e = lane; e < cap; e += 32) {
-    keys[e] = -1;
-    cnts[e] = 0;
+    v.keys[e] = -1;
+    v.cnts[e] = 0;
   }
   __syncwarp();
-  for (int t = 0; t < L; ++t) {
-    for (int64_t p = lo[t] + lane; p < hi[t]; p += 32) {
-      int32_t q = int32_t(__ldg(sj + int64_t(t) * N + p));
-      if (q != j) h_insert(keys, cnts, logc, q);
+  for (int t = 0; t < a.L; ++t) {
+    const uint32_t *ct = a.scls + int64_t(t) * a.ncls;
+    for (int32_t p = v.lo[t] + lane; p < v.hi[t]; p += 32) {
+      const int32_t B = int32_t(ct[p]);
+      if (B != A) h_insert(v.keys, v.cnts, v.logc, B);
     }
   }
   __syncwarp();
-  // compact (cnt desc, item asc) as ascending 64-bit keys
-  int n = 0;
+  int ncand = 0;
   for (int base = 0; base < cap; base += 32) {
     const int e = base + lane;
-    const bool occ = keys[e] != -1;
+    const bool occ = v.keys[e] != -1;
     const unsigned b = __ballot_sync(0xffffffffu, occ);
-    if (occ) list[n + __popc(b & lanemask_lt())] = (uint64_t(uint32_t(L - cnts[e])) << 32) | uint32_t(keys[e]);
-    n += __popc(b);
+    if (occ) {
+      const int q = ncand + __popc(b & lanemask_lt());
+      const int32_t B = v.keys[e];
+      v.cid[q] = B;
+      v.ccnt[q] = v.cnts[e];
+      v.head[q] = int32_t(a.cs[B]);
+      v.end[q] = int32_t(a.cs[B + 1]);
+    }
+    ncand += __popc(b);
   }
   __syncwarp();
-  int np = 1;
-  while (np < n) np <<= 1;
-  for (int e = n + lane; e < np; e += 32) list[e] = ~0ull;
-  __syncwarp();
-  for (int k = 2; k <= np; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int idx = lane; idx < np; idx += 32) {
-        const int ixj = idx ^ jj;
-        if (ixj > idx) {
-          const uint64_t a = list[idx], b = list[ixj];
-          const bool asc = (idx & k) == 0;
-          if ((a > b) == asc) {
-            list[idx] = b;
-            list[ixj] = a;
-          }
+  int32_t *out = a.rest + A * a.K;
+  int got = 0;
+  for (int level = a.L - 1; level >= 1 && got < need;) {
+    int32_t best = 0x7fffffff, bi = -1;
+    for (int e = lane; e < ncand; e += 32) {
+      if (v.ccnt[e] == level && v.head[e] < v.end[e]) {
+        const int32_t j = int32_t(a.members[v.head[e]]);
+        if (j < best) {
+          best = j;
+          bi = e;
         }
       }
-      __syncwarp();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int32_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob < best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (bi < 0) {
+      --level;
+      continue;
+    }
+    if (lane == 0) {
+      out[got] = best;
+      v.head[bi] += 1;
+    }
+    ++got;
+    __syncwarp();
   }
-  const int take = min(K, n);
-  for (int k = lane; k < take; k += 32) nbr[j * K + k] = int32_t(list[k] & 0xffffffffu);
-  // fill with the smallest items that are neither j nor candidates
-  int filled = take;
-  for (int64_t base = 0; filled < K && base < N; base += 32) {
-    const int64_t q = base + lane;
-    const bool ok = q < N && q != j && !h_contains(keys, logc, int32_t(q));
+  for (int64_t base = 0; got < need && base < a.N; base += 32) {
+    const int64_t j = base + lane;
+    bool ok = false;
+    if (j < a.N) {
+      const int32_t B = a.class_of[j];
+      ok = B != A && !h_contains(v.keys, v.logc, B);
+    }
     const unsigned b = __ballot_sync(0xffffffffu, ok);
-    const int pos = filled + __popc(b & lanemask_lt());
-    if (ok && pos < K) nbr[j * K + pos] = int32_t(q);
-    filled += __popc(b);
+    const int pos = got + __popc(b & lanemask_lt());
+    if (ok && pos < need) out[pos] = int32_t(j);
+    got += __popc(b);
   }
   __syncwarp();
 }
 
 __global__ void __launch_bounds__(32 * TK_WARPS)
-k_topk_smem(const uint32_t *sig, const uint64_t *skeys, const uint32_t *sj, int64_t N, int L, int bits,
-            int K, int32_t *nbr, int32_t *ovf_list, int32_t *ovf_n, int64_t *ovf_max) {
+k_topk_classes(ClassArgs a, int32_t *ovf_list, int32_t *ovf_n, int32_t *ovf_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TopkSmem &S = reinterpret_cast<TopkSmem *>(smem_raw)[threadIdx.x >> 5];
+  TopkWarp &S = reinterpret_cast<TopkWarp *>(smem_raw)[threadIdx.x >> 5];
+  TopkView v{S.keys, S.cnts, S.cid, S.ccnt, S.head, S.end, S.lo, S.hi, TK_LOGC};
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * TK_WARPS;
-  for (int64_t j = int64_t(blockIdx.x) * TK_WARPS + (threadIdx.x >> 5); j < N; j += nw) {
-    int64_t tot = 0;
-    for (int t = lane; t < L; t += 32) {
-      const uint64_t key = (uint64_t(t) << bits) | sig[int64_t(t) * N + j];
-      const uint64_t *kt = skeys + int64_t(t) * N;
-      S.lo[t] = lower_bound_u64(kt, N, key);
-      S.hi[t] = lower_bound_u64(kt, N, key + 1);
-      tot += S.hi[t] - S.lo[t] - 1;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    __syncwarp();
-    if (2 * tot > TK_HC) {   // too many candidates for the warp table: defer
+  for (int64_t A = int64_t(blockIdx.x) * TK_WARPS + (threadIdx.x >> 5); A < a.ncls; A += nw) {
+    const int64_t size = a.cs[A + 1] - a.cs[A];
+    const int own = int(min(int64_t(a.K), size - 1));
+    const int need = a.K - own;
+    if (need == 0) continue;
+    const int32_t tot = class_bucket_ranges(a, A, S.lo, S.hi);
+    if (2 * tot > TK_HC) {          // more candidate classes than the shared table holds
       if (lane == 0) {
-        int slot = atomicAdd(ovf_n, 1);
-        ovf_list[slot] = int32_t(j);
-        atomicMax(reinterpret_cast<unsigned long long *>(ovf_max), (unsigned long long)tot);
+        ovf_list[atomicAdd(ovf_n, 1)] = int32_t(A);
+        atomicMax(ovf_max, tot);
       }
       continue;
     }
-    topk_item(j, sig, skeys, sj, N, L, bits, K, S.keys, S.cnts, S.list, S.lo, S.hi, 10, nbr);
+    class_rank(a, A, need, v);
   }
 }
 
-// Items whose candidate total exceeds the shared table: one warp per item with
-// a table of 2^logc entries in global scratch.
-__global__ void k_topk_global(const uint32_t *sig, const uint64_t *skeys, const uint32_t *sj, int64_t N, int L,
-                              int bits, int K, int32_t *nbr, const int32_t *ovf_list, int32_t novf, int logc,
-                              int32_t *gkeys, int32_t *gcnts, uint64_t *glist, int64_t *glohi) {
-  const int lane = threadIdx.x & 31;
+// Classes deferred by k_topk_classes: one warp each, tables in global scratch
+// (per warp: keys and counts of 2^logc entries, four candidate arrays of half
+// that, and the 2 x 64 bucket bounds).
+__global__ void k_topk_classes_global(ClassArgs a, const int32_t *ovf_list, int32_t novf, int logc,
+                                      int32_t *scratch) {
   const int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   const int64_t cap = int64_t(1) << logc;
-  int32_t *keys = gkeys + w * cap;
-  int32_t *cnts = gcnts + w * cap;
-  uint64_t *list = glist + w * cap;
-  int64_t *lo = glohi + w * 128, *hi = lo + 64;
+  int32_t *base = scratch + w * (4 * cap + 128);
+  TopkView g{base,           base + cap,           base + 2 * cap,       base + 2 * cap + cap / 2,
+             base + 3 * cap, base + 3 * cap + cap / 2, base + 4 * cap, base + 4 * cap + 64, logc};
   for (int64_t x = w; x < novf; x += nw) {
-    const int64_t j = ovf_list[x];
-    for (int t = lane; t < L; t += 32) {
-      const uint64_t key = (uint64_t(t) << bits) | sig[int64_t(t) * N + j];
-      const uint64_t *kt = skeys + int64_t(t) * N;
-      lo[t] = lower_bound_u64(kt, N, key);
-      hi[t] = lower_bound_u64(kt, N, key + 1);
-    }
-    __syncwarp();
-    topk_item(j, sig, skeys, sj, N, L, bits, K, keys, cnts, list, lo, hi, logc, nbr);
+    const int64_t A = ovf_list[x];
+    const int need = a.K - int(min(int64_t(a.K), a.cs[A + 1] - a.cs[A] - 1));
+    class_bucket_ranges(a, A, g.lo, g.hi);
+    class_rank(a, A, need, g);
   }
 }
+
+__global__ void k_write_rows(const int32_t *class_of, const int32_t *pos_of, const int64_t *cs,
+                             const uint32_t *members, const int32_t *rest, int64_t N, int K, int32_t *nbr) {
+  const int64_t n = N * K;
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = x / K;
+    const int k = int(x - j * K);
+    const int64_t A = class_of[j];
+    const int64_t c0 = cs[A];
+    const int own = int(min(int64_t(K), cs[A + 1] - c0 - 1));
+    if (k < own) {
+      const int64_t m = pos_of[j] - c0;       // j's place in its class
+      nbr[x] = int32_t(members[c0 + (k < m ? k : k + 1)]);
+    } else {
+      nbr[x] = rest[A * K + (k - own)];
+    }
+  }
+}
+
+__global__ void k_set_i64_s(int64_t *p, int64_t v) { *p = v; }
 
 lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc,
                               int64_t nnz, const uint64_t *H, int32_t *nbr, uint32_t *sig_out, cudaStream_t st) {
@@ -485,47 +604,71 @@ lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *
     LSHMF_TRY(dispatch_sig<int64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, st));
   if (sig_out)
     LSHMF_CUDA(h, cudaMemcpyAsync(sig_out, sig, sizeof(uint32_t) * c.L * N, cudaMemcpyDeviceToDevice, st));
-  // --- buckets: sort (t, key) -> item
-  const int64_t n = int64_t(c.L) * N;
-  LSHMF_TRY(ensure(h, h->tmp[1], n * sizeof(uint64_t), "bucket keys"));
-  LSHMF_TRY(ensure(h, h->tmp[2], n * sizeof(uint64_t), "bucket keys (sorted)"));
-  LSHMF_TRY(ensure(h, h->tmp[3], n * sizeof(uint32_t) * 2, "bucket items"));
+
+  // --- classes of identical keys: sort items by a 64-bit hash of their L keys
+  const int64_t nL = int64_t(c.L) * N;
+  LSHMF_TRY(ensure(h, h->tmp[1], nL * sizeof(uint64_t) + 64, "class keys"));
+  LSHMF_TRY(ensure(h, h->tmp[2], nL * sizeof(uint64_t) + 64, "class keys (sorted)"));
+  LSHMF_TRY(ensure(h, h->tmp[3], nL * sizeof(uint32_t) * 2 + 64, "class values"));
+  const size_t arena = N * 4 * 2 + (N + 1) * 8 * 3 + N * 4 + 256;
+  LSHMF_TRY(ensure(h, h->tmp[4], arena, "class tables"));
   uint64_t *k0 = h->tmp[1].as<uint64_t>(), *k1 = h->tmp[2].as<uint64_t>();
-  uint32_t *v0 = h->tmp[3].as<uint32_t>(), *v1 = v0 + n;
-  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8L * h->num_sms);
-  LSHMF_LAUNCH(h, k_bucket_keys, gn, 256, 0, st, sig, N, c.L, c.bits, k0, v0);
-  LSHMF_TRY(radix_sort_pairs(h, k0, v0, k1, v1, n, c.bits + std::max(1, bits_for(c.L)), st));
-  // --- top-K
-  int32_t *ovf = reinterpret_cast<int32_t *>(units);          // reuse: N int32 + counter + max
-  int32_t *ovf_n = ovf + N;
-  int64_t *ovf_max = reinterpret_cast<int64_t *>(unit_start);  // unit_start no longer needed
-  LSHMF_CUDA(h, cudaMemsetAsync(ovf_n, 0, sizeof(int32_t), st));
-  LSHMF_CUDA(h, cudaMemsetAsync(ovf_max, 0, sizeof(int64_t), st));
-  const size_t smem = sizeof(TopkSmem) * TK_WARPS;
-  LSHMF_CUDA(h, cudaFuncSetAttribute(k_topk_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const unsigned gt = (unsigned)std::min<int64_t>(ceil_div(N, TK_WARPS), 4L * h->num_sms);
-  LSHMF_LAUNCH(h, k_topk_smem, gt, 32 * TK_WARPS, smem, st, sig, k1, v1, N, c.L, c.bits, c.K, nbr, ovf, ovf_n,
-               ovf_max);
-  int32_t novf = 0;
-  int64_t maxtot = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&novf, ovf_n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaMemcpyAsync(&maxtot, ovf_max, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
-  if (novf > 0) {
-    int logc = 1;
-    while ((int64_t(1) << logc) < 2 * maxtot + 2) ++logc;
-    const int64_t nwarps = std::min<int64_t>(novf, 2L * h->num_sms * 8);
-    const int64_t cap = int64_t(1) << logc;
-    const size_t need = nwarps * (cap * (4 + 4 + 8) + 128 * 8);
-    LSHMF_TRY(ensure(h, h->tmp[4], need, "top-K overflow tables"));
-    char *base = h->tmp[4].as<char>();
-    int32_t *gk = reinterpret_cast<int32_t *>(base);
-    int32_t *gc = gk + nwarps * cap;
-    uint64_t *gl = reinterpret_cast<uint64_t *>(gc + nwarps * cap);
-    int64_t *glh = reinterpret_cast<int64_t *>(gl + nwarps * cap);
-    LSHMF_LAUNCH(h, k_topk_global, (unsigned)ceil_div(nwarps, 8), 256, 0, st, sig, k1, v1, N, c.L, c.bits, c.K, nbr,
-                 ovf, novf, logc, gk, gc, gl, glh);
+  uint32_t *v0 = h->tmp[3].as<uint32_t>(), *v1 = v0 + nL;
+  char *ar = h->tmp[4].as<char>();
+  int32_t *class_of = reinterpret_cast<int32_t *>(ar);
+  int32_t *pos_of = class_of + N;
+  int64_t *cs = reinterpret_cast<int64_t *>(ar + ((N * 8 + 15) & ~int64_t(15)));
+  int64_t *flag = cs + (N + 1);
+  int64_t *fscan = flag + (N + 1);
+  uint32_t *members = reinterpret_cast<uint32_t *>(fscan + (N + 1));
+  const unsigned gN = (unsigned)std::min<int64_t>(ceil_div(N, 256), 8L * h->num_sms);
+  int64_t ncls = 0;
+  for (int attempt = 0;; ++attempt) {
+    if (attempt == 8) return set_err(h, LSHMF_ECUDA, "build_neighbours: key hash kept colliding");
+    LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
+    LSHMF_LAUNCH(h, k_sig_hash, gN, 256, 0, st, sig, N, c.L, 0x9E3779B97F4A7C15ull * uint64_t(attempt + 1), k0, v0);
+    LSHMF_TRY(radix_sort_pairs(h, k0, v0, k1, members, N, 64, st));
+    LSHMF_LAUNCH(h, k_class_flags, gN, 256, 0, st, k1, members, sig, N, c.L, flag, h->d_err);
+    int32_t herr = 0;
+    LSHMF_CUDA(h, cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st));
+    LSHMF_CUDA(h, cudaStreamSynchronize(st));
+    if (!(herr & DERR_HASH)) break;
   }
+  LSHMF_TRY(exclusive_scan_i64(h, flag, fscan, N, st));
+  LSHMF_LAUNCH(h, k_class_emit, gN, 256, 0, st, flag, fscan, members, N, class_of, pos_of, cs);
+  LSHMF_CUDA(h, cudaMemcpyAsync(&ncls, fscan + N, 8, cudaMemcpyDeviceToHost, st));
+  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+
+  // --- per-table buckets of classes: sort (t, key) -> class
+  const int64_t n = int64_t(c.L) * ncls;
+  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8L * h->num_sms);
+  LSHMF_LAUNCH(h, k_class_bucket_keys, gn, 256, 0, st, sig, members, cs, N, ncls, c.L, c.bits, k0, v0);
+  LSHMF_TRY(radix_sort_pairs(h, k0, v0, k1, v1, n, c.bits + std::max(1, bits_for(c.L)), st));
+
+  // --- top-K: rank other classes per class, then write every item's row
+  LSHMF_TRY(ensure(h, h->tmp[5], sizeof(int32_t) * (ncls * c.K + ncls + 64), "top-K rest lists"));
+  int32_t *rest = h->tmp[5].as<int32_t>();
+  int32_t *ovf = rest + ncls * c.K;
+  int32_t *ovf_ctr = reinterpret_cast<int32_t *>(h->d_red);   // [0] count, [1] max candidates
+  LSHMF_CUDA(h, cudaMemsetAsync(ovf_ctr, 0, 8, st));
+  ClassArgs a{sig, k1, v1, members, cs, class_of, N, ncls, c.L, c.bits, c.K, rest};
+  const size_t smem = sizeof(TopkWarp) * TK_WARPS;
+  LSHMF_CUDA(h, cudaFuncSetAttribute(k_topk_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned gt = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ncls, TK_WARPS), 8L * h->num_sms));
+  LSHMF_LAUNCH(h, k_topk_classes, gt, 32 * TK_WARPS, smem, st, a, ovf, ovf_ctr, ovf_ctr + 1);
+  int32_t hovf[2] = {0, 0};
+  LSHMF_CUDA(h, cudaMemcpyAsync(hovf, ovf_ctr, 8, cudaMemcpyDeviceToHost, st));
+  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  if (hovf[0] > 0) {
+    int logc = 1;
+    while ((int64_t(1) << logc) < 2 * int64_t(hovf[1]) + 2) ++logc;
+    const int64_t cap = int64_t(1) << logc;
+    const int64_t grid = std::min<int64_t>(ceil_div(hovf[0], 8), h->num_sms);
+    LSHMF_TRY(ensure(h, h->aux, sizeof(int32_t) * grid * 8 * (4 * cap + 128) + 64, "top-K overflow tables"));
+    LSHMF_LAUNCH(h, k_topk_classes_global, (unsigned)grid, 256, 0, st, a, ovf, hovf[0], logc, h->aux.as<int32_t>());
+  }
+  LSHMF_LAUNCH(h, k_write_rows, (unsigned)std::min<int64_t>(ceil_div(N * c.K, 256), 16L * h->num_sms), 256, 0, st,
+               class_of, pos_of, cs, members, rest, N, c.K, nbr);
   return LSHMF_OK;
 }
 

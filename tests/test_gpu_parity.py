@@ -233,10 +233,31 @@ def test_mid_small_one_epoch(mid_small):
     compare_params(p, po, what="mid@0.02 epoch 0")
 
 
+def test_degenerate_keys_sampled_rows():
+    """Yahoo!-shaped values at 1 % of the users: 625k items but 2.5M ratings, so
+    most items have no rater (all-ones keys, one huge class of identical keys)
+    and many share a single rater.  Signatures are checked in full, J^K on
+    sampled rows against the all-pairs definition."""
+    w = synth.scaled(synth.LARGE, 0.01)
+    r = Run(w)
+    col_ptr, row, rr = oracle.csc(w.M, w.N, r.d["train_i"], r.d["train_j"], r.d["train_r"])
+    sig = oracle.signatures(w.M, w.N, w.L, w.bits, w.psi_pow, col_ptr, row, rr, r.d["H"])
+    assert np.array_equal(r.sig.cpu().numpy().view(np.uint32), sig)
+    cnt = np.diff(col_ptr)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([np.flatnonzero(cnt == 0)[:8], np.flatnonzero(cnt == 1)[:8], np.flatnonzero(cnt > 50)[:8],
+                           rng.choice(w.N, 8, replace=False), [0, w.N - 1]]).astype(np.int32)
+    g = r.nbr.cpu().numpy()
+    assert np.array_equal(g[rows], oracle.topk_rows(sig, w.K, rows))
+
+
 @pytest.fixture(scope="module")
 def large_small():
-    """Yahoo!-shaped values (0..100, Psi = r^4, int64 sums) on 625k items (wide index path)."""
-    w = synth.scaled(synth.LARGE, 0.01)
+    """Yahoo!-shaped values (0..100, Psi = r^4, int64 sums), F = 128, K = 32,
+    32 tables x 16 bits, on 40,000 items (above the 32,768 of the wide index
+    path) and 20,000 users, 5M ratings."""
+    from dataclasses import replace
+    w = replace(synth.scaled(synth.LARGE, 0.02), N=40_000, nnz=5_000_000, P=64, name="large-shape 20kx40k")
     r = Run(w)
     r.orc_csc, r.orc_sig, r.orc_nbr = oracle_nbr(w, r.d)
     return r

@@ -463,3 +463,11 @@ def test_loss_regularisers_closed_form():
 def test_splitmix_published_outputs():
     for idx, hexval in read_golden("splitmix64_seed0.txt"):
         assert synth.splitmix_at(0, int(idx)) == int(hexval, 16)
+
+
+def test_topk_rows_equal_bruteforce():
+    rng = np.random.default_rng(11)
+    sig = rng.integers(0, 4, size=(5, 60)).astype(np.uint32)
+    full = oracle.topk_bruteforce(sig, 7)
+    rows = np.array([0, 13, 59, 27], dtype=np.int32)
+    assert np.array_equal(oracle.topk_rows(sig, 7, rows), full[rows])
