@@ -129,6 +129,11 @@ def scaled(w: Workload, frac: float, name: str | None = None, **kw) -> Workload:
     return replace(w, name=name or f"{w.name}@{frac:g}", M=M, nnz=min(nnz, M * w.N), **kw)
 
 
+# Netflix-shaped at a quarter of the users and ratings (120k x 17,770, 25M):
+# inputs still larger than L2, small enough for full-counter profiles.
+WORKLOADS["mid-quarter"] = scaled(MID, 0.25, name="mid-quarter-120kx17770-25M")
+
+
 def generate(w: Workload, threads: int = 0) -> dict:
     """Generate the workload's ratings, split, hash bits and initial parameters.
 
