@@ -189,6 +189,24 @@ lshmf_status lshmf_rmse(lshmf_handle *h, const lshmf_params *p, const int32_t *d
                         const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,
                         void *stream);
 
+/* lshmf_rmse without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- a
+ * process whose device memory is fully reserved up front by a pool or
+ * caching allocator, or a latency-critical loop that must not stall on
+ * cudaMalloc/cudaFree.  Same arguments and result as lshmf_rmse (equal
+ * within FP64 rounding: the partial sums are grouped differently).
+ * Scratch: a fixed array compiled into the library (128 KiB + 8 bytes), held
+ * on every GPU that loads the library until the process exits.  Limit:
+ * 1 <= n <= 33,554,432 query pairs; larger n returns LSHMF_EINVAL.  The
+ * first call on a device looks up the array's device address (the device
+ * must be current and be the handle's device); make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on
+ * the GPU (other streams, other host threads) race: serialise them.
+ * Synchronous; requires lshmf_prepare_training. */
+lshmf_status lshmf_rmse_noalloc(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users,
+                                const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

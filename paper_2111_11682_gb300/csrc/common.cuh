@@ -124,6 +124,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Query pairs reduced by one CTA of the caller-scratch RMSE (train.cu).
+constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;
+
 // ---- sort / scan primitives (sort.cu) ----
 // Stable LSD radix sort of (key, val) pairs on key bits [0, nbits).  Results
 // end in keys_out/vals_out.  keys_in/vals_in are used as ping-pong space and

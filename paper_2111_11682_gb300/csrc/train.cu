@@ -840,4 +840,24 @@ lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int
   return LSHMF_OK;
 }
 
+// The RMSE of rmse() with device scratch supplied by the caller: one CTA per
+// RMSE_PAIRS_PER_CTA query pairs, `scratch` holds one partial sum per CTA plus
+// the total (at least ceil(n / RMSE_PAIRS_PER_CTA) + 1 doubles).
+lshmf_status rmse_with_scratch(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj,
+                               const uint8_t *qr, int64_t n, double *scratch, int64_t scratch_len, double *h_rmse,
+                               cudaStream_t st) {
+  if (!h->tl.ready) return set_err(h, LSHMF_ESTATE, "rmse: lshmf_prepare_training has not succeeded");
+  if (n <= 0) return set_err(h, LSHMF_EINVAL, "rmse: n must be positive");
+  const int64_t ctas = ceil_div(n, RMSE_PAIRS_PER_CTA);
+  if (ctas + 1 > scratch_len) return set_err(h, LSHMF_EINVAL, "rmse: scratch too small");
+  LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
+  LSHMF_LAUNCH(h, k_sqerr, (unsigned)ctas, 256, 0, st, pred_args(h, p), qi, qj, qr, n, scratch);
+  LSHMF_LAUNCH(h, k_sum_f64, 1, 256, 0, st, scratch, ctas, scratch + ctas);
+  double s = 0.0;
+  LSHMF_CUDA(h, cudaMemcpyAsync(&s, scratch + ctas, 8, cudaMemcpyDeviceToHost, st));
+  LSHMF_TRY(check_device_flag(h, st, "rmse"));
+  *h_rmse = double(h->cfg.rating_scale) * std::sqrt(s / double(n));
+  return LSHMF_OK;
+}
+
 }  // namespace lshmf

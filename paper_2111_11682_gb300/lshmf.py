@@ -20,7 +20,8 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 # Every entry point declared in include/lshmf.h.
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
-           "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse"]
+           "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
+           "lshmf_rmse_noalloc"]
 
 
 class LshmfError(RuntimeError):
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
         "lshmf_training_stats": ([P, ctypes.POINTER(TrainStats)], ctypes.c_int),
         "lshmf_predict": ([P, CP, P, P, I64, P, P], ctypes.c_int),
         "lshmf_rmse": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_rmse_noalloc": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -243,6 +245,15 @@ class LshMF:
         out = ctypes.c_double(0.0)
         self._chk(self.lib.lshmf_rmse(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), _ptr(r), users.numel(),
                                       ctypes.byref(out), _stream(stream)))
+        return out.value
+
+
+    def rmse_noalloc(self, p: Params, users, items, r, stream=None) -> float:
+        """lshmf_rmse_noalloc: same result as rmse() without any device allocation."""
+        cp = p._c()
+        out = ctypes.c_double(0.0)
+        self._chk(self.lib.lshmf_rmse_noalloc(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), _ptr(r),
+                                              users.numel(), ctypes.byref(out), _stream(stream)))
         return out.value
 
 
