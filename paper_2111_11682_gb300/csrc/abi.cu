@@ -61,7 +61,8 @@ lshmf_status lshmf_create(const lshmf_config *cfg, lshmf_handle **out) {
   Handle *h = &hh->h;
   h->cfg = *cfg;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
     delete hh;
     return LSHMF_ECUDA;
   }

@@ -44,7 +44,7 @@ struct TrainLayout {
   int32_t max_users_per_block = 0;
   int32_t max_segs_per_block = 0;
   int32_t mask_words = 0;          // ceil(K / 32)
-  DevBuf sr;        // uint32 [nnz]: user slot (low 16) | rank in block (high 16)
+  DevBuf sr;        // uint32 [nnz]: user slot (bits 0-15) | rank in block (16-30) | last-in-block (31)
   DevBuf rat;       // uint8  [nnz]: rating
   DevBuf mask;      // uint32 [nnz * mask_words]: bit k = J^K[j][k] in R(i)
   DevBuf roff;      // int64  [nnz + 1]: offset of the rating's packed neighbour values
@@ -69,6 +69,7 @@ struct Handle {
   lshmf_config cfg;
   int device = 0;
   int num_sms = 0;
+  int smem_optin = 0;   // opt-in shared memory per block (bytes)
   std::string last_error;
   int32_t *d_err = nullptr;     // device error flag (sticky until prepare)
   double *d_red = nullptr;      // small reduction output

@@ -24,8 +24,6 @@
 
 namespace lshmf {
 
-constexpr int SPIN_LIMIT = 1 << 22;
-
 // ------------------------------------------------------------ helpers ----
 __global__ void k_keys_ij(const int32_t *ii, const int32_t *jj, int64_t nnz, int64_t M, int64_t N, int ibits,
                           uint64_t *keys, uint32_t *vals, int32_t *err) {
@@ -149,8 +147,9 @@ __global__ void k_slot_rank(const uint64_t *kU, const uint32_t *vU, const int64_
     const int64_t blk = int64_t(kU[x] >> ibits);
     const int64_t slot = rid - blk_user[blk];
     const int64_t rank = x - run_pos[rid];
-    if (slot > 0xffff || rank > 0xffff) atomicOr(err, DERR_CAPACITY);
-    sr[vU[x]] = uint32_t(slot & 0xffff) | (uint32_t(rank & 0xffff) << 16);
+    const bool last = (x + 1 == nnz) || flag[x + 1];    // the user's last rating in this block
+    if (slot > 0xffff || rank > 0x7fff) atomicOr(err, DERR_CAPACITY);
+    sr[vU[x]] = uint32_t(slot & 0xffff) | (uint32_t(rank & 0x7fff) << 16) | (last ? 0x80000000u : 0u);
   }
 }
 
@@ -415,7 +414,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   LSHMF_CUDA(h, cudaMemcpyAsync(hred, red, 32, cudaMemcpyDeviceToHost, st));
   LSHMF_CUDA(h, cudaStreamSynchronize(st));
   tl.npacked = npacked;
-  LSHMF_TRY(ensure(h, tl.packed, npacked + 16, "layout packed neighbour ratings"));
+  LSHMF_TRY(ensure(h, tl.packed, npacked + 64, "layout packed neighbour ratings"));
   if (wide) {
     LSHMF_CUDA(h, cudaFuncSetAttribute(k_index<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
     LSHMF_LAUNCH(h, (k_index<1, true>), gi, IDX_THREADS, ismem, st, tl.user_ptr.as<int64_t>(),
@@ -441,200 +440,6 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   return LSHMF_OK;
 }
 
-// ------------------------------------------------------------- SGD ----
-struct SgdArgs {
-  const uint32_t *sr;
-  const uint8_t *rat;
-  const uint32_t *mask;
-  const uint8_t *packed;
-  const int32_t *seg_j;
-  const int64_t *seg_p0;
-  const int64_t *seg_roff;
-  const int64_t *blk_seg;
-  const int64_t *blk_user;
-  const int32_t *users;
-  const float *bh0n;
-  double *seg_sq;
-  float *U, *V, *b, *bh, *W, *C;
-  float mu, inv_scale;
-  float gam[6], lam[6];
-  int F, K, P, mw, maxu;
-  int32_t *err;
-};
-
-constexpr int SGD_WARPS = 8;
-
-__device__ __forceinline__ int ld_acquire_cta(const int *p) {
-  cuda::atomic_ref<const int, cuda::thread_scope_block> a(*p);
-  return a.load(cuda::memory_order_acquire);
-}
-__device__ __forceinline__ void st_release_cta(int *p, int v) {
-  cuda::atomic_ref<int, cuda::thread_scope_block> a(*p);
-  a.store(v, cuda::memory_order_release);
-}
-
-template <int FPL, int KPL>
-__global__ void __launch_bounds__(32 * SGD_WARPS)
-k_sgd_stratum(const SgdArgs a, int s) {
-  extern __shared__ __align__(16) int smem_i[];
-  const int lane = threadIdx.x & 31;
-  const int P = a.P;
-  const int q = blockIdx.x;
-  const int64_t blk = int64_t(q) * P + (q + s) % P;
-  const int64_t sg0 = a.blk_seg[blk], sg1 = a.blk_seg[blk + 1];
-  if (sg0 == sg1) return;
-  const int64_t u0 = a.blk_user[blk];
-  const int nu = int(a.blk_user[blk + 1] - u0);
-  int *cnt = smem_i;
-  int *users = smem_i + a.maxu;
-  int *ctl = users + a.maxu;   // [0] next segment, [1] abort
-  for (int x = threadIdx.x; x < nu; x += blockDim.x) {
-    cnt[x] = 0;
-    users[x] = a.users[u0 + x];
-  }
-  if (threadIdx.x == 0) {
-    ctl[0] = 0;
-    ctl[1] = 0;
-  }
-  __syncthreads();
-  const int F = a.F, K = a.K, mw = a.mw;
-  const float mu = a.mu, isc = a.inv_scale;
-  const float g_b = a.gam[0], g_bh = a.gam[1], g_u = a.gam[2], g_v = a.gam[3], g_w = a.gam[4], g_c = a.gam[5];
-  const float l_b = a.lam[0], l_bh = a.lam[1], l_u = a.lam[2], l_v = a.lam[3], l_w = a.lam[4], l_c = a.lam[5];
-  while (true) {
-    int sgo = 0;
-    if (lane == 0) sgo = atomicAdd(&ctl[0], 1);
-    sgo = __shfl_sync(0xffffffffu, sgo, 0);
-    const int64_t sg = sg0 + sgo;
-    if (sg >= sg1) break;
-    const int32_t j = a.seg_j[sg];
-    const int64_t p0 = a.seg_p0[sg], p1 = a.seg_p0[sg + 1];
-    int64_t roff = a.seg_roff[sg];
-    float v[FPL], w[KPL], c[KPL], bn[KPL];
-#pragma unroll
-    for (int f = 0; f < FPL; ++f) {
-      const int idx = lane + 32 * f;
-      v[f] = idx < F ? a.V[int64_t(j) * F + idx] : 0.f;
-    }
-#pragma unroll
-    for (int kk = 0; kk < KPL; ++kk) {
-      const int k = lane + 32 * kk;
-      const bool ok = k < K;
-      w[kk] = ok ? a.W[int64_t(j) * K + k] : 0.f;
-      c[kk] = ok ? a.C[int64_t(j) * K + k] : 0.f;
-      bn[kk] = ok ? a.bh0n[int64_t(j) * K + k] : 0.f;
-    }
-    float bh = a.bh[j];
-    double sq = 0.0;
-    for (int64_t p = p0; p < p1; ++p) {
-      const uint32_t sr = a.sr[p];
-      const int slot = int(sr & 0xffffu), rank = int(sr >> 16);
-      const float r = float(a.rat[p]) * isc;
-      uint32_t m[KPL];
-      int nR = 0;
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        m[kk] = kk < mw ? a.mask[p * mw + kk] : 0u;
-        nR += __popc(m[kk]);
-      }
-      float rv[KPL];
-      bool ex[KPL];
-      int below = 0;
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        ex[kk] = (m[kk] >> lane) & 1u;
-        rv[kk] = ex[kk] ? float(a.packed[roff + below + __popc(m[kk] & lanemask_lt())]) * isc : 0.f;
-        below += __popc(m[kk]);
-      }
-      const int nN = K - nR;
-      // wait until the user's earlier ratings in this block are done
-      if (rank > 0) {
-        int it = 0;
-        while (ld_acquire_cta(&cnt[slot]) != rank) {
-          if (++it > SPIN_LIMIT || *((volatile int *)&ctl[1])) {
-            if (lane == 0) {
-              atomicOr(a.err, DERR_TIMEOUT);
-              ctl[1] = 1;
-            }
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-      const int32_t i = users[slot];
-      float u[FPL];
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) {
-        const int idx = lane + 32 * f;
-        u[f] = idx < F ? a.U[int64_t(i) * F + idx] : 0.f;
-      }
-      const float bi = a.b[i];
-      const float sR = nR > 0 ? rsqrtf(float(nR)) : 0.f;
-      const float sN = nN > 0 ? rsqrtf(float(nN)) : 0.f;
-      float dot = 0.f, pe = 0.f, pc = 0.f;
-      float x[KPL];
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) dot = fmaf(u[f], v[f], dot);
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        const bool ok = lane + 32 * kk < K;
-        x[kk] = rv[kk] - (mu + bi + bn[kk]);
-        if (ex[kk]) pe = fmaf(x[kk], w[kk], pe);
-        else if (ok) pc += c[kk];
-      }
-      const float S = warp_sum(dot + sR * pe + sN * pc);
-      const float e = r - (mu + bi + bh + S);
-      // Eq. (5), simultaneous: every right-hand side uses pre-step values
-      const float bi_n = bi + g_b * (e - l_b * bi);
-      bh = bh + g_bh * (e - l_bh * bh);
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) {
-        const int idx = lane + 32 * f;
-        const float un = u[f] + g_u * (e * v[f] - l_u * u[f]);
-        v[f] = v[f] + g_v * (e * u[f] - l_v * v[f]);
-        if (idx < F) a.U[int64_t(i) * F + idx] = un;
-      }
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        const bool ok = lane + 32 * kk < K;
-        if (ex[kk]) w[kk] = w[kk] + g_w * (sR * e * x[kk] - l_w * w[kk]);
-        else if (ok) c[kk] = c[kk] + g_c * (sN * e - l_c * c[kk]);
-      }
-      if (lane == 0) {
-        a.b[i] = bi_n;
-        sq += double(e) * double(e);
-      }
-      __threadfence_block();
-      __syncwarp();
-      if (lane == 0) st_release_cta(&cnt[slot], rank + 1);
-      roff += nR;
-    }
-#pragma unroll
-    for (int f = 0; f < FPL; ++f) {
-      const int idx = lane + 32 * f;
-      if (idx < F) a.V[int64_t(j) * F + idx] = v[f];
-    }
-#pragma unroll
-    for (int kk = 0; kk < KPL; ++kk) {
-      const int k = lane + 32 * kk;
-      if (k < K) {
-        a.W[int64_t(j) * K + k] = w[kk];
-        a.C[int64_t(j) * K + k] = c[kk];
-      }
-    }
-    if (lane == 0) {
-      a.bh[j] = bh;
-      a.seg_sq[sg] = sq;
-    }
-  }
-}
-
-__global__ void k_gather_bh0n(const float *bh0, const int32_t *nbr, int64_t n, float *bh0n) {
-  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n;
-       x += int64_t(gridDim.x) * blockDim.x)
-    bh0n[x] = bh0[nbr[x]];
-}
-
 // Fixed-order FP64 sum: each of 256 threads sums a strided slice, then a
 // fixed tree.  Deterministic for a given n.
 __global__ void k_sum_f64(const double *x, int64_t n, double *out) {
@@ -648,69 +453,6 @@ __global__ void k_sum_f64(const double *x, int64_t n, double *out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = s[0];
-}
-
-template <int FPL, int KPL>
-static lshmf_status launch_strata(Handle *h, const SgdArgs &a, int n_strata, cudaStream_t st) {
-  const size_t smem = size_t(2 * a.maxu + 4) * sizeof(int);
-  if (smem > 48 * 1024)
-    LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_stratum<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-  for (int s = 0; s < n_strata; ++s)
-    LSHMF_LAUNCH(h, (k_sgd_stratum<FPL, KPL>), a.P, 32 * SGD_WARPS, smem, st, a, s);
-  return LSHMF_OK;
-}
-
-lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
-                          cudaStream_t st) {
-  const lshmf_config &c = h->cfg;
-  TrainLayout &tl = h->tl;
-  if (!tl.ready) return set_err(h, LSHMF_ESTATE, "train: lshmf_prepare_training has not succeeded");
-  if (!p || !p->U || !p->V || !p->b || !p->bh || !p->W || !p->C)
-    return set_err(h, LSHMF_EINVAL, "train: null parameter pointer");
-  if (epoch < 0) return set_err(h, LSHMF_EINVAL, "train: epoch must be >= 0");
-  n_strata = std::min<int32_t>(std::max<int32_t>(n_strata, 0), c.P);
-  // bhat snapshot and the neighbours' snapshot values
-  LSHMF_CUDA(h, cudaMemcpyAsync(tl.bh0.p, p->bh, c.N * 4, cudaMemcpyDeviceToDevice, st));
-  LSHMF_LAUNCH(h, k_gather_bh0n, grid_for(h, c.N * c.K), 256, 0, st, tl.bh0.as<float>(), tl.nbr.as<int32_t>(),
-               c.N * c.K, tl.bh0n.as<float>());
-  if (h_sq) LSHMF_CUDA(h, cudaMemsetAsync(tl.seg_sq.p, 0, tl.nseg * 8, st));
-  SgdArgs a;
-  a.sr = tl.sr.as<uint32_t>();
-  a.rat = tl.rat.as<uint8_t>();
-  a.mask = tl.mask.as<uint32_t>();
-  a.packed = tl.packed.as<uint8_t>();
-  a.seg_j = tl.seg_j.as<int32_t>();
-  a.seg_p0 = tl.seg_p0.as<int64_t>();
-  a.seg_roff = tl.roff.as<int64_t>();
-  a.blk_seg = tl.blk_seg.as<int64_t>();
-  a.blk_user = tl.blk_user.as<int64_t>();
-  a.users = tl.users.as<int32_t>();
-  a.bh0n = tl.bh0n.as<float>();
-  a.seg_sq = tl.seg_sq.as<double>();
-  a.U = p->U; a.V = p->V; a.b = p->b; a.bh = p->bh; a.W = p->W; a.C = p->C;
-  a.mu = float(p->mu);
-  a.inv_scale = 1.0f / c.rating_scale;
-  const double tfac = 1.0 + double(c.beta) * std::pow(double(epoch), 1.5);   // Eq. (7)
-  for (int g = 0; g < 6; ++g) {
-    a.gam[g] = float(double(c.alpha[g]) / tfac);
-    a.lam[g] = c.lambda[g];
-  }
-  a.F = c.F; a.K = c.K; a.P = c.P; a.mw = tl.mask_words; a.maxu = std::max(1, tl.max_users_per_block);
-  a.err = h->d_err;
-  const int fpl = (c.F + 31) / 32, kpl = (c.K + 31) / 32;
-  lshmf_status s;
-  if (fpl <= 1) s = kpl <= 1 ? launch_strata<1, 1>(h, a, n_strata, st) : launch_strata<1, 2>(h, a, n_strata, st);
-  else if (fpl <= 2) s = kpl <= 1 ? launch_strata<2, 1>(h, a, n_strata, st) : launch_strata<2, 2>(h, a, n_strata, st);
-  else if (fpl <= 4) s = kpl <= 1 ? launch_strata<4, 1>(h, a, n_strata, st) : launch_strata<4, 2>(h, a, n_strata, st);
-  else s = kpl <= 1 ? launch_strata<8, 1>(h, a, n_strata, st) : launch_strata<8, 2>(h, a, n_strata, st);
-  LSHMF_TRY(s);
-  if (h_sq) {
-    LSHMF_LAUNCH(h, k_sum_f64, 1, 256, 0, st, tl.seg_sq.as<double>(), tl.nseg, h->d_red);
-    LSHMF_CUDA(h, cudaMemcpyAsync(h_sq, h->d_red, 8, cudaMemcpyDeviceToHost, st));
-    LSHMF_TRY(check_device_flag(h, st, "train"));
-  }
-  return LSHMF_OK;
 }
 
 // ------------------------------------------------------- predict / RMSE ----
