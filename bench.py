@@ -121,7 +121,7 @@ def traffic_from_profile(src_hash):
 
 def kernel_hash():
     h = hashlib.sha1()
-    for fn in ("train.cu", "common.cuh"):
+    for fn in ("sgd.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2111_11682_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -53,6 +53,7 @@ struct TrainLayout {
   DevBuf seg_p0;    // int64  [nseg + 1]: first rating of each run
   DevBuf blk_seg;   // int64  [P*P + 1]: first run of each block (block id = cb * P + rb)
   DevBuf blk_user;  // int64  [P*P + 1]: first entry of each block's user table
+  DevBuf blk_order; // int32  [P*P]: stratum s launches block (q, (q+s) mod P) as CTA x, q = blk_order[s*P + x]
   DevBuf users;     // int32  [sum of users per block]: slot -> user id
   DevBuf nbr;       // int32  [N * K]: copy of J^K
   DevBuf user_ptr;  // int64  [M + 1]: CSR of the training set by user (items ascending)
@@ -63,7 +64,7 @@ struct TrainLayout {
   DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
 };
 
-constexpr int PREP_BUFS = 22;
+constexpr int PREP_BUFS = 25;
 
 struct Handle {
   lshmf_config cfg;

@@ -274,6 +274,22 @@ __global__ void k_seg_roff(const int64_t *seg_p0, int64_t nseg, const int64_t *r
     seg_roff[s] = roff[seg_p0[s]];
 }
 
+// Launch order of each stratum: blocks by descending rating count (ties by q), so
+// that the longest blocks start in the first wave of CTAs.  The order only
+// decides when a block runs, never what it computes.
+__global__ void k_order_keys(const int64_t *blk_seg, const int64_t *seg_p0, int64_t P, uint64_t *keys,
+                             uint32_t *vals) {
+  const int64_t NB = P * P;
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < NB; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t s = x / P, q = x - s * P;
+    const int64_t blk = q * P + (q + s) % P;
+    const int64_t work = seg_p0[blk_seg[blk + 1]] - seg_p0[blk_seg[blk]];
+    const uint64_t lim = (uint64_t(1) << 40) - 1;
+    keys[x] = (uint64_t(s) << 40) | (lim - (uint64_t(work) < lim ? uint64_t(work) : lim));
+    vals[x] = uint32_t(q);
+  }
+}
+
 static unsigned grid_for(Handle *h, int64_t n, int per = 256) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, per), 16L * h->num_sms));
 }
@@ -305,7 +321,8 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
                                  size_t(nnz) * 8, size_t(nnz) * 4,                                   // kB vB
                                  size_t(n1) * 8, size_t(n1) * 8, size_t(nnz) * 8,                    // runs
                                  size_t(nnz) * 8, size_t(nnz) * 4,                                   // kU vU
-                                 size_t(nnz) * 4, size_t(n1) * 8, size_t(n1) * 8};                   // bposC cnt roff
+                                 size_t(nnz) * 4, size_t(n1) * 8, size_t(n1) * 8,                    // bposC cnt roff
+                                 size_t(NB) * 8, size_t(NB) * 4, size_t(NB) * 8};                    // block order
   for (int q = 0; q < PREP_BUFS; ++q) LSHMF_TRY(ensure(h, T[q], tsz[q] + 64, "prepare temporaries"));
   uint64_t *k0 = T[0].as<uint64_t>(), *k1 = T[1].as<uint64_t>();
   uint32_t *v0 = T[2].as<uint32_t>(), *v1 = T[3].as<uint32_t>();
@@ -429,6 +446,16 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   LSHMF_LAUNCH(h, k_seg_roff, grid_for(h, nseg), 256, 0, st, tl.seg_p0.as<int64_t>(), nseg, roff,
                tl.roff.as<int64_t>());
   LSHMF_TRY(check_device_flag(h, st, "prepare_training"));
+  // per-stratum launch order (heaviest blocks first)
+  LSHMF_TRY(ensure(h, tl.blk_order, NB * 4, "layout block order"));
+  {
+    uint64_t *ko = T[22].as<uint64_t>();
+    uint32_t *vo = T[23].as<uint32_t>();
+    LSHMF_LAUNCH(h, k_order_keys, grid_for(h, NB), 256, 0, st, tl.blk_seg.as<int64_t>(), tl.seg_p0.as<int64_t>(), P,
+                 ko, vo);
+    LSHMF_TRY(radix_sort_pairs(h, ko, vo, T[24].as<uint64_t>(), tl.blk_order.as<uint32_t>(), NB,
+                               40 + std::max(1, bits_for(P)), st));
+  }
   const unsigned long long maxseg = hred[1], maxusers = hred[2];
   if (maxusers > 65535)
     return set_err(h, LSHMF_EINVAL, "prepare_training: %llu users in one block (max 65535); raise P", maxusers);

@@ -111,7 +111,7 @@ TINY = Workload("tiny-2000x1000-100k", M=2000, N=1000, nnz=100_000, zipf_s=1.1, 
 MID = Workload("mid-480kx17770-100M", M=480_000, N=17_770, nnz=100_000_000, zipf_s=1.0,
                user_model=1, user_sigma=1.0, value_scale=5, test_frac=0.0142, F=64, K=64, L=16,
                bits=12, psi_pow=2, epochs=10, alpha=(0.02, 0.02, 0.02, 0.02, 0.001, 0.001),
-               lam=(0.01, 0.01, 0.01, 0.01, 0.05, 0.05), beta=0.3, rating_scale=1.0, P=304)
+               lam=(0.01, 0.01, 0.01, 0.01, 0.05, 0.05), beta=0.3, rating_scale=1.0, P=1216)
 
 # Yahoo!-Music-shaped values 0..100 (ratings / 20 for training, Sec. 5.1); Yahoo column.
 LARGE = Workload("large-1Mx625k-250M", M=1_000_000, N=625_000, nnz=250_000_000, zipf_s=1.2,
