@@ -87,7 +87,8 @@ void lshmf_destroy(lshmf_handle *hh) {
   release(h->aux);
   TrainLayout &t = h->tl;
   DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
-                    &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq};
+                    &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
+                          &t.seg_ck, &t.ck_roff, &t.next_blk};
   for (DevBuf *b : bufs) release(*b);
   cudaFree(h->d_err);
   cudaFree(h->d_red);
@@ -161,7 +162,8 @@ lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out
   for (const auto &b : h->tmp) bytes += b.bytes;
   for (const auto &b : h->prep) bytes += b.bytes;
   const DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
-                          &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq};
+                          &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
+                          &t.seg_ck, &t.ck_roff, &t.next_blk};
   for (const DevBuf *b : bufs) bytes += b->bytes;
   out->device_bytes = bytes + h->red_part.bytes;
   return LSHMF_OK;

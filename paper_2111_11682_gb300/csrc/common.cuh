@@ -62,6 +62,10 @@ struct TrainLayout {
   DevBuf bh0;       // float  [N]: bhat snapshot (per epoch)
   DevBuf bh0n;      // float  [N * K]: bhat snapshot of each item's neighbours
   DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
+  DevBuf seg_ck;    // int32  [nseg + 1]: first chunk of each run (chunks of SGD_CH ratings)
+  DevBuf ck_roff;   // int64  [chunks]: offset of each chunk's packed neighbour values
+  DevBuf next_blk;  // int32  [P]: blocks of each stratum taken so far (SGD scheduler)
+  int64_t nchunks = 0;
 };
 
 constexpr int PREP_BUFS = 25;
@@ -125,6 +129,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
+
+// Ratings per chunk of the SGD item chain (sgd.cu; the chunk layout is built by train.cu).
+constexpr int SGD_CH = 8;
 
 // Query pairs reduced by one CTA of the caller-scratch RMSE (train.cu).
 constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;

@@ -274,6 +274,23 @@ __global__ void k_seg_roff(const int64_t *seg_p0, int64_t nseg, const int64_t *r
     seg_roff[s] = roff[seg_p0[s]];
 }
 
+// Chunks of SGD_CH consecutive ratings inside each run: count per run, then
+// the first chunk of each run and the packed offset of each chunk.
+__global__ void k_seg_nck(const int64_t *seg_p0, int64_t nseg, int64_t *nck) {
+  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < nseg;
+       s += int64_t(gridDim.x) * blockDim.x)
+    nck[s] = ceil_div(seg_p0[s + 1] - seg_p0[s], SGD_CH);
+}
+__global__ void k_chunks(const int64_t *seg_p0, const int64_t *ck_scan, int64_t nseg, const int64_t *roff,
+                         int32_t *seg_ck, int64_t *ck_roff) {
+  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s <= nseg;
+       s += int64_t(gridDim.x) * blockDim.x) {
+    seg_ck[s] = int32_t(ck_scan[s]);
+    if (s < nseg)
+      for (int64_t k = 0; k < ck_scan[s + 1] - ck_scan[s]; ++k) ck_roff[ck_scan[s] + k] = roff[seg_p0[s] + SGD_CH * k];
+  }
+}
+
 // Launch order of each stratum: blocks by descending rating count (ties by q), so
 // that the longest blocks start in the first wave of CTAs.  The order only
 // decides when a block runs, never what it computes.
@@ -445,6 +462,21 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   }
   LSHMF_LAUNCH(h, k_seg_roff, grid_for(h, nseg), 256, 0, st, tl.seg_p0.as<int64_t>(), nseg, roff,
                tl.roff.as<int64_t>());
+  // chunk layout of the SGD item chain
+  {
+    int64_t *nck = fl, *ckscan = fs;   // free after (U)
+    LSHMF_LAUNCH(h, k_seg_nck, grid_for(h, nseg), 256, 0, st, tl.seg_p0.as<int64_t>(), nseg, nck);
+    LSHMF_TRY(exclusive_scan_i64(h, nck, ckscan, nseg, st));
+    int64_t nchunks = 0;
+    LSHMF_CUDA(h, cudaMemcpyAsync(&nchunks, ckscan + nseg, 8, cudaMemcpyDeviceToHost, st));
+    LSHMF_CUDA(h, cudaStreamSynchronize(st));
+    tl.nchunks = nchunks;
+    LSHMF_TRY(ensure(h, tl.seg_ck, (nseg + 1) * 4, "layout run chunks"));
+    LSHMF_TRY(ensure(h, tl.ck_roff, nchunks * 8 + 8, "layout chunk offsets"));
+    LSHMF_TRY(ensure(h, tl.next_blk, P * 4, "stratum block counters"));
+    LSHMF_LAUNCH(h, k_chunks, grid_for(h, nseg + 1), 256, 0, st, tl.seg_p0.as<int64_t>(), ckscan, nseg, roff,
+                 tl.seg_ck.as<int32_t>(), tl.ck_roff.as<int64_t>());
+  }
   LSHMF_TRY(check_device_flag(h, st, "prepare_training"));
   // per-stratum launch order (heaviest blocks first)
   LSHMF_TRY(ensure(h, tl.blk_order, NB * 4, "layout block order"));
