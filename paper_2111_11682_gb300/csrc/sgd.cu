@@ -54,15 +54,18 @@
 
 namespace lshmf {
 
-constexpr int SGD_SPIN_LIMIT = 1 << 22;
+constexpr int SGD_SPIN_LIMIT = 1 << 22;   // polls of a bounded spin (with back-off: well over a second)
+constexpr int SGD_WAIT_TRIES = 1 << 20;   // suspended tries of a bounded mbarrier wait
+constexpr unsigned SGD_SUSPEND_NS = 1000; // suspend-time hint of one try
 constexpr int CH = SGD_CH;    // ratings per chunk (the chunk layout of prepare_training uses the same size)
 constexpr int GP = 3;         // producer warps per group
 constexpr int NRING = 4;      // chunk buffers per group
-constexpr int GQN = 16;       // group segment list (ring)
+constexpr int GRAB = 1;       // segments a group takes from the CTA queue at once (at most)
+constexpr int GQN = 32;       // group segment list (ring)
 constexpr int MAX_GROUPS = 4;
 constexpr int MAX_SLOTS = 4;  // blocks in flight per CTA
 
-static_assert(NRING > 1 && GQN >= NRING + GP + 2, "group segment ring too small");
+static_assert(NRING > 1 && GQN >= NRING + GP + GRAB + 2, "group segment ring too small");
 
 // Decay tables: row g of pow holds q_g^m, of inv q_g^-m (m = 0..CH), g = bh, v, w, c.
 enum { QT_BH = 0, QT_V = 1, QT_W = 2, QT_C = 3 };
@@ -79,9 +82,9 @@ struct SgdArgs {
   const int64_t *blk_seg;
   const int64_t *blk_user;
   const int32_t *order;
+  int32_t *next_blk;         // per stratum: blocks taken (zeroed per epoch)
   const int32_t *users;
   const float *bh0n;
-  int32_t *next_blk;         // per stratum: blocks taken (zeroed per epoch)
   double *seg_sq;
   float *U, *V, *b, *bh, *W, *C;
   float mu, inv_scale;
@@ -113,7 +116,7 @@ enum : int32_t { FL_FIRST = 1, FL_LAST = 2, FL_END = 4 };
 
 // One chunk handed from a producer to its group's consumer: n <= CH ratings of
 // one item.  Row strides are padded by 4 floats; columns past F (u) and past
-// K (aw, ac, gx) hold zeros.
+// K (aw, ac) hold zeros.
 template <int FPL, int KPL>
 struct __align__(16) Chunk {
   static constexpr int FS = 32 * FPL + 4;
@@ -121,12 +124,13 @@ struct __align__(16) Chunk {
   alignas(16) float u[CH][FS];    // user rows u_i
   alignas(16) float aw[CH][KS];   // Aw[t][k]
   alignas(16) float ac[CH][KS];   // Ac[t][k]
-  alignas(16) float gx[CH][KS];   // g_w |R_t|^-1/2 x_tk for k in R_t, else 0 (w update coefficient)
   float T[CH][CH];      // (I + L)^-1, lower triangular with unit diagonal
   float d[CH];          // r - (mu + b_i)
   float b[CH];          // user bias b_i
-  float gc[CH];         // g_c |N_t|^-1/2 (0 for an empty N_t)
+  float sR[CH], sN[CH]; // |R_t|^-1/2, |N_t|^-1/2 (0 for an empty set and past n)
+  float gc[CH];         // g_c |N_t|^-1/2
   uint32_t m[CH][2];    // explicit-neighbour masks
+  int32_t off[CH];      // first packed neighbour rating of rating t inside pk (bytes)
   int32_t i[CH];        // user ids
   int32_t rel[CH];      // user counter index (slot * maxu + user slot), or -1 past n
   int32_t relv[CH];     // value that releases the user (its rank in the block + 1)
@@ -139,29 +143,48 @@ struct __align__(16) Chunk {
   alignas(16) uint32_t pk[CH * 8 * KPL + 4];   // packed neighbour ratings (from a 4-byte aligned start)
 };
 
-// 16-byte copies land in u, v, w, c: their offsets must be multiples of 16.
+// 16-byte accesses land in u, aw, ac, v, w, c: their offsets must be multiples of 16.
 template <int FPL, int KPL>
 constexpr bool chunk_aligned() {
   using X = Chunk<FPL, KPL>;
   return offsetof(X, u) % 16 == 0 && offsetof(X, aw) % 16 == 0 && offsetof(X, ac) % 16 == 0 &&
-         offsetof(X, gx) % 16 == 0 && offsetof(X, v) % 16 == 0 && offsetof(X, w) % 16 == 0 &&
-         offsetof(X, c) % 16 == 0 && offsetof(X, pk) % 16 == 0 && sizeof(X) % 16 == 0 &&
-         (X::FS * 4) % 16 == 0;
+         offsetof(X, v) % 16 == 0 && offsetof(X, w) % 16 == 0 && offsetof(X, c) % 16 == 0 &&
+         offsetof(X, pk) % 16 == 0 && sizeof(X) % 16 == 0 && (X::FS * 4) % 16 == 0 && (X::KS * 4) % 16 == 0;
 }
 static_assert(chunk_aligned<1, 1>() && chunk_aligned<1, 2>() && chunk_aligned<2, 1>() && chunk_aligned<2, 2>() &&
                   chunk_aligned<4, 1>() && chunk_aligned<4, 2>() && chunk_aligned<8, 1>() && chunk_aligned<8, 2>(),
-              "chunk layout: 16-byte copy targets misaligned");
+              "chunk layout: 16-byte access targets misaligned");
+
+// Per-producer scratch of the build: Qw, Qc and L.
+template <int KPL>
+struct __align__(16) Scratch {
+  static constexpr int KS = 32 * KPL + 4;
+  alignas(16) float qw[CH][KS];
+  alignas(16) float qc[CH][KS];
+  float L[CH][CH];
+};
+
+// A segment (one item's run of ratings inside a block) as the CTA queue and
+// the groups hold it.
+struct SegInfo {
+  int seg;      // segment id
+  int slot;     // block slot of its block
+  int j;        // item
+  int p0;       // first rating (blocked order)
+  int n;        // ratings
+  int ck0;      // first chunk (chunk layout)
+  int nck;      // chunks
+  int pad;
+};
 
 template <int FPL, int KPL>
 struct __align__(16) Group {
   Chunk<FPL, KPL> ring[NRING];
-  float L[GP][CH][CH];   // producer scratch
-  int ready[NRING];      // position p is in ring[p % NRING] once ready[p % NRING] == p + 1
-  int freed[NRING];      // ring[x] may take position p once freed[x] == p / NRING
-  int seg[GQN];          // the group's e-th segment (ring)
-  int slot[GQN];         // its block slot
+  Scratch<KPL> scr[GP];
+  uint64_t full[NRING];  // phase k completes when position k * NRING + x is in ring[x] (32 arrivals)
+  uint64_t empty[NRING]; // phase k completes when the consumer is done with position k * NRING + x
+  SegInfo ent[GQN];      // the group's e-th segment (ring)
   int start[GQN];        // stream position of its first chunk
-  int nck[GQN];          // its chunk count
   int ngrab;             // segments taken
   int endpos;            // stream position after the last segment taken
   int done;              // no more segments
@@ -173,19 +196,18 @@ struct CtaCtl {
   int abort_;
   int pad[3];
   int slot_left[MAX_SLOTS];   // segments of the slot's block not finished (0 = slot free)
-  int slot_base[MAX_SLOTS];   // first segment id of the slot's block
+  int slot_pad[MAX_SLOTS];
 };
 
 struct Smem {
   CtaCtl *ctl;
   float (*qt)[CH + 1];
-  int *cq;          // [cqn] segment ids (CTA queue, ring)
-  int8_t *cqs;      // [cqn] their block slots
+  SegInfo *cq;      // [cqn] CTA queue (ring)
   int *users;       // [nslots][maxu]
   int *cnt;         // [nslots][maxu]
 };
 
-__device__ __forceinline__ bool sgd_abort(const SgdArgs &a, CtaCtl *ctl) {
+__device__ __noinline__ bool sgd_abort(const SgdArgs &a, CtaCtl *ctl) {
   if ((threadIdx.x & 31) == 0) {
     atomicOr(a.err, DERR_TIMEOUT);
     st_rel(&ctl->abort_, 1);
@@ -194,12 +216,39 @@ __device__ __forceinline__ bool sgd_abort(const SgdArgs &a, CtaCtl *ctl) {
   return false;
 }
 
-// Bounded spin until *p == want (all lanes read the same word).
-__device__ __forceinline__ bool spin_eq(const SgdArgs &a, const int *p, int want, CtaCtl *ctl) {
+// Polling back-off: a few tight polls, then sleeps growing to 256 ns.
+__device__ __forceinline__ void backoff(int it) {
+  if (it > 8) __nanosleep(it > 64 ? 256u : (it > 24 ? 128u : 32u));
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Every lane of the warp arrives (the barriers count 32 arrivals per phase),
+// so each lane's earlier shared-memory writes are released by its own arrive.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(SGD_SUSPEND_NS)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the completion of the phase of the given parity: the warp
+// is suspended in hardware between tries (no polling instructions issued).
+__device__ __forceinline__ bool mbar_wait(const SgdArgs &a, uint64_t *bar, unsigned parity, CtaCtl *ctl) {
   int it = 0;
-  while (ld_acq(p) != want) {
-    if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
-    if (it > 16) __nanosleep(20);
+  while (!mbar_try(bar, parity)) {
+    if (++it > SGD_WAIT_TRIES || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
   }
   return true;
 }
@@ -212,7 +261,7 @@ __device__ __forceinline__ bool lock_warp(const SgdArgs &a, int *l, CtaCtl *ctl)
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) break;
     if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
-    if (it > 16) __nanosleep(20);
+    backoff(it);
   }
   __threadfence_block();
   return true;
@@ -223,87 +272,105 @@ __device__ __forceinline__ void unlock_warp(int *l) {
 }
 
 // ------------------------------------------------------- CTA block queue ----
-// Takes the stratum's next block, loads its user table into a free slot and
-// appends its segments to the queue.  Called with cq_lock held and the queue
-// empty.  Returns false on abort.
-__device__ bool refill(const SgdArgs &a, const Smem &sm, int s) {
+// The scheduler warp of a CTA takes the stratum's blocks from a global counter
+// (heaviest first).  For each block it waits for a free block slot and room in
+// the queue, loads the block's user table into the slot and appends the
+// block's segments, with their item, rating range and chunks, to the queue.
+__device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, int s) {
   const int lane = threadIdx.x & 31;
   CtaCtl *ctl = sm.ctl;
   while (true) {
     int bi = 0;
     if (lane == 0) bi = atomicAdd(&a.next_blk[s], 1);
     bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (bi >= a.P) {
-      if (lane == 0) st_rel(&ctl->cq_done, 1);
-      __syncwarp();
-      return true;
-    }
+    if (bi >= a.P) break;
     const int q = a.order[int64_t(s) * a.P + bi];
     const int64_t blk = int64_t(q) * a.P + (q + s) % a.P;
-    const int64_t sg0 = a.blk_seg[blk], sg1 = a.blk_seg[blk + 1];
+    const int sg0 = int(a.blk_seg[blk]), sg1 = int(a.blk_seg[blk + 1]);
     if (sg0 == sg1) continue;
     const int64_t u0 = a.blk_user[blk];
     const int nu = int(a.blk_user[blk + 1] - u0);
-    // a free slot (slots are released by the consumers of their blocks' last segments)
+    const int ns = sg1 - sg0;
+    // a free slot (released by the consumer of its block's last segment) and queue room
     int slot = -1, it = 0;
-    while (slot < 0) {
-      if (lane == 0)
-        for (int x = 0; x < a.nslots; ++x)
-          if (ld_acq(&ctl->slot_left[x]) == 0) {
-            slot = x;
-            break;
-          }
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (slot < 0) {
-        if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
-        if (it > 16) __nanosleep(50);
+    const int tail = ctl->cq_tail;
+    while (true) {
+      if (lane == 0) {
+        slot = -1;
+        if (tail + ns - ld_acq(&ctl->cq_head) <= a.cqn)
+          for (int x = 0; x < a.nslots; ++x)
+            if (ld_acq(&ctl->slot_left[x]) == 0) {
+              slot = x;
+              break;
+            }
       }
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot >= 0) break;
+      if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+        sgd_abort(a, ctl);
+        return;
+      }
+      backoff(it);
     }
     int *us = sm.users + slot * a.maxu, *cn = sm.cnt + slot * a.maxu;
     for (int x = lane; x < nu; x += 32) {
       us[x] = a.users[u0 + x];
       cn[x] = 0;
     }
-    const int ns = int(sg1 - sg0);
-    const int tail = ctl->cq_tail;
     for (int x = lane; x < ns; x += 32) {
-      sm.cq[(tail + x) % a.cqn] = int(sg0 + x);
-      sm.cqs[(tail + x) % a.cqn] = int8_t(slot);
+      const int sg = sg0 + x;
+      SegInfo e;
+      e.seg = sg;
+      e.slot = slot;
+      e.j = a.seg_j[sg];
+      const int64_t p0 = a.seg_p0[sg];
+      e.p0 = int(p0);
+      e.n = int(a.seg_p0[sg + 1] - p0);
+      e.ck0 = a.seg_ck[sg];
+      e.nck = a.seg_ck[sg + 1] - e.ck0;
+      e.pad = 0;
+      sm.cq[(tail + x) % a.cqn] = e;
     }
     __syncwarp();
     if (lane == 0) {
-      ctl->slot_base[slot] = int(sg0);
       ctl->slot_left[slot] = ns;
       __threadfence_block();
       st_rel(&ctl->cq_tail, tail + ns);
     }
     __syncwarp();
-    return true;
   }
+  if (lane == 0) st_rel(&ctl->cq_done, 1);
 }
 
-// Takes the next CTA queue entry for a group (its segment and block slot are
-// read under the queue lock, before a refill can reuse the entry): 0, or -1
-// when the stratum has no more blocks for this CTA, or -2 on abort.
-__device__ int take_entry(const SgdArgs &a, const Smem &sm, int s, int &sg, int &sl) {
+// Takes up to maxn of the next CTA queue entries for a group and copies them
+// to dst[(base + x) % GQN] under the queue lock (before the scheduler can reuse
+// them).  Returns how many (waiting for at least one), 0 when this CTA has no
+// more blocks in the stratum, or -2 on abort.
+__device__ __noinline__ int take_entries(const SgdArgs &a, const Smem &sm, SegInfo *dst, int base, int maxn) {
   CtaCtl *ctl = sm.ctl;
+  const int lane = threadIdx.x & 31;
   if (!lock_warp(a, &ctl->cq_lock, ctl)) return -2;
-  int e = -1;
+  int got = 0, it = 0;
+  const int h = ctl->cq_head;
   while (true) {
-    const int h = ctl->cq_head, t = ctl->cq_tail;
+    const int done = ld_acq(&ctl->cq_done);   // read before the tail: a done scheduler has appended everything
+    const int t = ld_acq(&ctl->cq_tail);
     if (h < t) {
-      e = 0;
-      sg = sm.cq[h % a.cqn];
-      sl = sm.cqs[h % a.cqn];
+      got = min(maxn, t - h);
+      if (lane < got) dst[(base + lane) % GQN] = sm.cq[(h + lane) % a.cqn];
       __syncwarp();
-      if ((threadIdx.x & 31) == 0) ctl->cq_head = h + 1;
+      if (lane == 0) st_rel(&ctl->cq_head, h + got);
       break;
     }
-    if (ctl->cq_done) break;
-    if (!refill(a, sm, s)) return -2;
+    if (done) break;
+    if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+      sgd_abort(a, ctl);
+      return -2;
+    }
+    backoff(it);
   }
   unlock_warp(&ctl->cq_lock);
-  return e;
+  return got;
 }
 
 // ------------------------------------------------------------- producer ----
@@ -321,7 +388,7 @@ struct Producer {
   // Makes sure stream position pos is covered by a taken segment.  Returns
   // 1 when it is, 0 when the group's stream ends before pos, -1 on abort.
   // The group lock is only tried: while another producer holds it (possibly
-  // waiting inside refill for a block slot to free up), this producer keeps
+  // waiting for the CTA queue), this producer keeps
   // re-reading endpos, so a position that is already covered is never held
   // up behind the lock.
   __device__ int cover(int pos) {
@@ -339,32 +406,31 @@ struct Producer {
           sgd_abort(a, ctl);
           return -1;
         }
-        if (it > 16) __nanosleep(20);
+        backoff(it);
         continue;
       }
       __threadfence_block();
       if (pos >= G.endpos && !G.done) {
-        int sg = 0, sl = 0;
-        const int e = take_entry(a, sm, s, sg, sl);
-        if (e == -2) {
+        const int g = G.ngrab;
+        const int got = take_entries(a, sm, G.ent, g, GRAB);
+        if (got == -2) {
           unlock_warp(&G.lock);
           return -1;
         }
         const int lane = threadIdx.x & 31;
-        if (e < 0) {
-          if (lane == 0) st_rel(&G.done, 1);
-        } else {
-          const int nck = a.seg_ck[sg + 1] - a.seg_ck[sg];
-          const int g = G.ngrab, st = G.endpos;
-          __syncwarp();
-          if (lane == 0) {
-            G.seg[g % GQN] = sg;
-            G.slot[g % GQN] = sl;
-            G.start[g % GQN] = st;
-            G.nck[g % GQN] = nck;
-            G.ngrab = g + 1;
+        __syncwarp();
+        if (lane == 0) {
+          if (got == 0) {
+            st_rel(&G.done, 1);
+          } else {
+            int st = G.endpos;
+            for (int x = 0; x < got; ++x) {
+              G.start[(g + x) % GQN] = st;
+              st += G.ent[(g + x) % GQN].nck;
+            }
+            G.ngrab = g + got;
             __threadfence_block();
-            st_rel(&G.endpos, st + nck);
+            st_rel(&G.endpos, st);
           }
         }
       }
@@ -376,13 +442,14 @@ struct Producer {
   __device__ bool end(int pos) {
     const int lane = threadIdx.x & 31;
     Chunk<FPL, KPL> &C = G.ring[pos % NRING];
-    if (!spin_eq(a, &G.freed[pos % NRING], pos / NRING, sm.ctl)) return false;
+    const int k = pos / NRING;
+    if (k > 0 && !mbar_wait(a, &G.empty[pos % NRING], (k - 1) & 1, sm.ctl)) return false;
     if (lane == 0) {
       C.flags = FL_END;
       C.n = 0;
     }
     __syncwarp();
-    if (lane == 0) st_rel(&G.ready[pos % NRING], pos + 1);
+    mbar_arrive(&G.full[pos % NRING]);
     return true;
   }
 
@@ -390,16 +457,14 @@ struct Producer {
   __device__ bool produce(int pos) {
     const int lane = threadIdx.x & 31, F = a.F, K = a.K;
     CtaCtl *ctl = sm.ctl;
-    while (!(pos < G.start[cur % GQN] + G.nck[cur % GQN])) ++cur;
+    while (!(pos < G.start[cur % GQN] + G.ent[cur % GQN].nck)) ++cur;
+    const SegInfo E = G.ent[cur % GQN];
     const int k = pos - G.start[cur % GQN];
-    const int nk = G.nck[cur % GQN];
-    const int sg = G.seg[cur % GQN];
-    const int slot = G.slot[cur % GQN];
+    const int nk = E.nck, sg = E.seg, slot = E.slot;
     // chunk metadata (one rating per lane) and neighbour baselines
-    const int32_t j = a.seg_j[sg];
-    const int64_t p0 = a.seg_p0[sg], p1 = a.seg_p0[sg + 1];
-    const int64_t c0 = p0 + int64_t(k) * CH;
-    const int n = int(min(int64_t(CH), p1 - c0));
+    const int32_t j = E.j;
+    const int64_t c0 = int64_t(E.p0) + int64_t(k) * CH;
+    const int n = min(CH, E.n - k * CH);
     uint32_t sr = 0, rr = 0, m0 = 0, m1 = 0;
     if (lane < n) {
       const int64_t x = c0 + lane;
@@ -408,7 +473,7 @@ struct Producer {
       m0 = a.mask[x * a.mw];
       if (KPL > 1 && a.mw > 1) m1 = a.mask[x * a.mw + 1];
     }
-    const int64_t roff = a.ck_roff[a.seg_ck[sg] + k];
+    const int64_t roff = a.ck_roff[E.ck0 + k];
     float bn[KPL];
 #pragma unroll
     for (int kk = 0; kk < KPL; ++kk) {
@@ -416,7 +481,7 @@ struct Producer {
       bn[kk] = kx < K ? a.bh0n[int64_t(j) * K + kx] : 0.f;
     }
     Chunk<FPL, KPL> &C = G.ring[pos % NRING];
-    if (!spin_eq(a, &G.freed[pos % NRING], pos / NRING, ctl)) return false;
+    if (pos >= NRING && !mbar_wait(a, &G.empty[pos % NRING], ((pos / NRING) - 1) & 1, ctl)) return false;
     if (k == 0) {
       // item state for the consumer (Alg. 3 reads v_j, bhat_j, w_j, c_j once per item)
       const float *vs = a.V + int64_t(j) * F, *ws = a.W + int64_t(j) * K, *cs = a.C + int64_t(j) * K;
@@ -449,7 +514,7 @@ struct Producer {
           cp_async_wait_all();
           return sgd_abort(a, ctl);
         }
-        if (it > 16) __nanosleep(20);
+        backoff(it);
       }
     }
     __syncwarp();   // every lane's copies below follow the acquires of the lanes that polled
@@ -488,17 +553,18 @@ struct Producer {
     cp_async_commit();
     // per-rating scalars that do not need the copies
     const bool act = lane < n;
-    const float r_l = float(rr) * a.inv_scale;
     const float sR_l = act && nr > 0 ? rsqrtf(float(nr)) : 0.f;
     const float sN_l = act && (K - nr) > 0 ? rsqrtf(float(K - nr)) : 0.f;
-    const int off_l = sh + incl - nr;
     if (lane < CH) {
       C.i[lane] = i;
       C.rel[lane] = act ? slot * a.maxu + us : -1;
       C.relv[lane] = rank + 1;
       C.m[lane][0] = m0;
       C.m[lane][1] = m1;
+      C.sR[lane] = sR_l;
+      C.sN[lane] = sN_l;
       C.gc[lane] = a.gam[5] * sN_l;
+      C.off[lane] = sh + incl - nr;
     }
     if (lane == 0) {
       C.n = n;
@@ -509,112 +575,87 @@ struct Producer {
     }
     cp_async_wait_all();
     __syncwarp();
-    const float b_l = lane < n ? C.b[lane] : 0.f;
-    if (lane < CH) C.d[lane] = act ? r_l - (a.mu + b_l) : 0.f;
-    build(C, m0, m1, b_l, sR_l, sN_l, off_l, n, bn);
-    // publish: the warp's writes are ordered before lane 0's release
+    if (lane < CH) C.d[lane] = act ? float(rr) * a.inv_scale - (a.mu + C.b[lane]) : 0.f;
     __syncwarp();
-    if (lane == 0) st_rel(&G.ready[pos % NRING], pos + 1);
+    build(C, n, bn);
+    // publish: every lane releases its own writes
+    __syncwarp();
+    mbar_arrive(&G.full[pos % NRING]);
     return true;
   }
 
-  // Builds Aw, Ac, gx, L and T of a staged chunk (its copies have landed).
-  __device__ void build(Chunk<FPL, KPL> &C, uint32_t m0_l, uint32_t m1_l, float b_l, float sR_l, float sN_l,
-                        int off_l, int n, const float (&bn)[KPL]) {
+  // Builds Aw, Ac, L and T of a staged chunk (its copies have landed).
+  __device__ void build(Chunk<FPL, KPL> &C, int n, const float (&bn)[KPL]) {
     const int lane = threadIdx.x & 31, K = a.K;
     const float(*qt)[CH + 1] = sm.qt;
-    const float g_bh = a.gam[1], g_v = a.gam[3], g_w = a.gam[4], g_c = a.gam[5];
     const float qw1 = qt[QT_W][1], qwi1 = qt[4 + QT_W][1], qc1 = qt[QT_C][1], qci1 = qt[4 + QT_C][1];
     const uint8_t *pk = reinterpret_cast<const uint8_t *>(C.pk);
-    float part[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) part[q] = 0.f;
+    Scratch<KPL> &X = G.scr[p];
+    // phase 1, lane <-> neighbour k: x_tk, Aw, Qw, Ac, Qc along the chunk (decays carried as running products)
 #pragma unroll
     for (int kk = 0; kk < KPL; ++kk) {
-      const bool valid = lane + 32 * kk < K;
-      float awv[CH], qwv[CH], acv[CH], qcv[CH];
+      const int kx = lane + 32 * kk;
+      const bool valid = kx < K;
       float pw = 1.f, pwi = qwi1, pc = 1.f, pci = qci1;   // q_w^a, q_w^-(a+1), q_c^(t-a), q_c^-(t-a+1)
-#pragma unroll
-      for (int t = 0; t < CH; ++t) {
-        const uint32_t m0 = __shfl_sync(0xffffffffu, m0_l, t);
-        const uint32_t mk = kk == 0 ? m0 : __shfl_sync(0xffffffffu, m1_l, t);
-        const float bt = __shfl_sync(0xffffffffu, b_l, t);
-        const float sR = __shfl_sync(0xffffffffu, sR_l, t), sN = __shfl_sync(0xffffffffu, sN_l, t);
-        const int off = __shfl_sync(0xffffffffu, off_l, t);
+#pragma unroll 1
+      for (int t = 0; t < n; ++t) {
+        const uint32_t m0 = C.m[t][0];
+        const uint32_t mk = kk == 0 ? m0 : C.m[t][1];
         const bool ex = (mk >> lane) & 1u;
         const bool nx = !ex && valid;
         const int below = (kk == 0 ? 0 : __popc(m0)) + __popc(mk & lanemask_lt());
-        const float r8 = float(pk[ex ? off + below : 0]);
-        const float xv = ex ? r8 * a.inv_scale - (a.mu + bt + bn[kk]) : 0.f;
-        const float sx = sR * xv;
-        awv[t] = ex ? sx * pw : 0.f;
-        qwv[t] = ex ? sx * pwi : 0.f;
-        acv[t] = nx ? sN * pc : 0.f;
-        qcv[t] = nx ? sN * pci : 0.f;
-        const int kx = lane + 32 * kk;
-        C.aw[t][kx] = awv[t];
-        C.ac[t][kx] = acv[t];
-        C.gx[t][kx] = ex ? g_w * sx : 0.f;
+        const float r8 = float(pk[ex ? C.off[t] + below : 0]);
+        const float xv = ex ? r8 * a.inv_scale - (a.mu + C.b[t] + bn[kk]) : 0.f;
+        const float sx = C.sR[t] * xv, sN = C.sN[t];
+        C.aw[t][kx] = ex ? sx * pw : 0.f;
+        X.qw[t][kx] = ex ? sx * pwi : 0.f;
+        C.ac[t][kx] = nx ? sN * pc : 0.f;
+        X.qc[t][kx] = nx ? sN * pci : 0.f;
         pw = ex ? pw * qw1 : pw;
         pwi = ex ? pwi * qwi1 : pwi;
         pc = ex ? pc : pc * qc1;
         pci = ex ? pci : pci * qci1;
       }
-      int q = 0;
-#pragma unroll
-      for (int t = 1; t < CH; ++t) {
-        const float at = g_w * awv[t], ct = g_c * acv[t];
-#pragma unroll
-        for (int m = 0; m < t; ++m, ++q) part[q] = fmaf(at, qwv[m], fmaf(ct, qcv[m], part[q]));
-      }
     }
-    // Gram of the user rows over this lane's features (rows past n read as zero)
-    {
-      float ut[CH][FPL];
-#pragma unroll
-      for (int t = 0; t < CH; ++t)
-#pragma unroll
-        for (int f = 0; f < FPL; ++f) ut[t][f] = t < n ? C.u[t][lane * FPL + f] : 0.f;
-      int q = 0;
-#pragma unroll
-      for (int t = 1; t < CH; ++t)
-#pragma unroll
-        for (int m = 0; m < t; ++m, ++q) {
-          float g = 0.f;
-#pragma unroll
-          for (int f = 0; f < FPL; ++f) g = fmaf(ut[t][f], ut[m][f], g);
-          part[q] = fmaf(g_v * qt[QT_V][t - 1 - m], g, part[q]);
-        }
-    }
-    // transposed reduction: lane q ends with the warp sum of part[q]
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-      const bool hi = lane & w;
-#pragma unroll
-      for (int q = 0; q < w; ++q) {
-        const float send = hi ? part[q] : part[q + w], keep = hi ? part[q + w] : part[q];
-        part[q] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-      }
-    }
-    float(*L)[CH] = G.L[p];
+    __syncwarp();
+    // phase 2, lane <-> pair (t, m), m < t < n: the strictly lower entries of L
     if (lane < CH * (CH - 1) / 2) {
       int t = 1, m = lane;
       while (m >= t) {
         m -= t;
         ++t;
       }
-      L[t][m] = part[0] + g_bh * qt[QT_BH][t - 1 - m];
+      if (t < n) {
+        float sw = 0.f, sc = 0.f, su = 0.f;
+#pragma unroll 2
+        for (int q = 0; q < 8 * KPL; ++q) {
+          const float4 at = *reinterpret_cast<const float4 *>(&C.aw[t][4 * q]);
+          const float4 qm = *reinterpret_cast<const float4 *>(&X.qw[m][4 * q]);
+          const float4 ct = *reinterpret_cast<const float4 *>(&C.ac[t][4 * q]);
+          const float4 cm = *reinterpret_cast<const float4 *>(&X.qc[m][4 * q]);
+          sw = fmaf(at.x, qm.x, fmaf(at.y, qm.y, fmaf(at.z, qm.z, fmaf(at.w, qm.w, sw))));
+          sc = fmaf(ct.x, cm.x, fmaf(ct.y, cm.y, fmaf(ct.z, cm.z, fmaf(ct.w, cm.w, sc))));
+        }
+#pragma unroll 2
+        for (int q = 0; q < 8 * FPL; ++q) {
+          const float4 ut = *reinterpret_cast<const float4 *>(&C.u[t][4 * q]);
+          const float4 um = *reinterpret_cast<const float4 *>(&C.u[m][4 * q]);
+          su = fmaf(ut.x, um.x, fmaf(ut.y, um.y, fmaf(ut.z, um.z, fmaf(ut.w, um.w, su))));
+        }
+        X.L[t][m] = a.gam[4] * sw + a.gam[5] * sc + a.gam[3] * qt[QT_V][t - 1 - m] * su +
+                    a.gam[1] * qt[QT_BH][t - 1 - m];
+      }
     }
     __syncwarp();
-    // T = (I + L)^-1 by columns, lane <-> column
-    if (lane < CH) {
+    // T = (I + L)^-1 by columns, lane <-> column (rows at or past n are never read)
+    if (lane < n) {
       float col[CH];
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
         float acc = 0.f;
 #pragma unroll
-        for (int m = 0; m < t; ++m) acc = fmaf(L[t][m], col[m], acc);
-        col[t] = t == lane ? 1.f : (t > lane ? -acc : 0.f);
+        for (int m = 0; m < t; ++m) acc = fmaf(X.L[t][m], col[m], acc);
+        col[t] = t == lane ? 1.f : (t > lane && t < n ? -acc : 0.f);
         C.T[t][lane] = col[t];
       }
     }
@@ -642,15 +683,13 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
   const int lane = threadIdx.x & 31, F = a.F, K = a.K;
   CtaCtl *ctl = sm.ctl;
   const float(*qt)[CH + 1] = sm.qt;
-  const float g_b = a.gam[0], g_bh = a.gam[1], g_u = a.gam[2], g_v = a.gam[3];
+  const float g_b = a.gam[0], g_bh = a.gam[1], g_u = a.gam[2], g_v = a.gam[3], g_w = a.gam[4];
   // decay terms gamma*lambda*x are applied as fmaf(-gl, x, x): one rounding
   // relative to x per step (a rounded 1 - gamma*lambda factor would bias every
   // step the same way and compound over an item's ratings)
   const float gl_b = g_b * a.lam[0], gl_bh = g_bh * a.lam[1], gl_u = g_u * a.lam[2];
-  const float gl_v = g_v * a.lam[3], gl_w = a.gam[4] * a.lam[4], gl_c = a.gam[5] * a.lam[5];
-  float qv[CH];
-#pragma unroll
-  for (int t = 0; t < CH; ++t) qv[t] = qt[QT_V][t];
+  const float gl_v = g_v * a.lam[3], gl_w = g_w * a.lam[4], gl_c = a.gam[5] * a.lam[5];
+  const float qwi1 = qt[4 + QT_W][1];
   float v[FPL], w[KPL], c[KPL];
   float bh = 0.f, sqf = 0.f;
   double sq = 0.0;
@@ -660,7 +699,7 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
   for (int kk = 0; kk < KPL; ++kk) w[kk] = c[kk] = 0.f;
   for (int pos = 0;; ++pos) {
     const int buf = pos % NRING;
-    if (!spin_eq(a, &G.ready[buf], pos + 1, ctl)) return;
+    if (!mbar_wait(a, &G.full[buf], (pos / NRING) & 1, ctl)) return;
     const Chunk<FPL, KPL> &C = G.ring[buf];
     const int flags = C.flags;
     if (flags & FL_END) break;
@@ -683,20 +722,16 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
       sqf = 0.f;
     }
     // base: lane partials of q_v^t u_t.v + Aw_t.w + Ac_t.c for every t of the chunk
-    float uu[CH][FPL];
     float pt[CH];
 #pragma unroll
     for (int t = 0; t < CH; ++t) {
       float du = 0.f, dk = 0.f;
 #pragma unroll
-      for (int f = 0; f < FPL; ++f) {
-        uu[t][f] = C.u[t][lane * FPL + f];
-        du = fmaf(uu[t][f], v[f], du);
-      }
+      for (int f = 0; f < FPL; ++f) du = fmaf(C.u[t][lane * FPL + f], v[f], du);
 #pragma unroll
       for (int kk = 0; kk < KPL; ++kk)
         dk = fmaf(C.aw[t][lane + 32 * kk], w[kk], fmaf(C.ac[t][lane + 32 * kk], c[kk], dk));
-      pt[t] = fmaf(qv[t], du, dk);
+      pt[t] = fmaf(qt[QT_V][t], du, dk);
     }
     // transposed reduction: lane l ends with the warp sum for t = (l >> 2) & 7
     {
@@ -720,62 +755,58 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
     }
     const int tl = (lane >> 2) & 7;
     const float y_l = tl < n ? C.d[tl] - (qt[QT_BH][tl] * bh + pt[0]) : 0.f;
-    float e[CH];
+    // e = T y; lane t keeps e_t
+    float e_l = 0.f;
     {
       float y[CH];
 #pragma unroll
       for (int t = 0; t < CH; ++t) y[t] = __shfl_sync(0xffffffffu, y_l, 4 * t);
+      const int tt = lane & 7;
+      float acc = 0.f;
 #pragma unroll
-      for (int t = 0; t < CH; ++t) {
-        float acc = y[t];
-#pragma unroll
-        for (int m = 0; m < t; ++m) acc = fmaf(C.T[t][m], y[m], acc);
-        e[t] = t < n ? acc : 0.f;
-      }
+      for (int m = 0; m < CH; ++m) acc = fmaf(m <= tt ? C.T[tt][m] : 0.f, y[m], acc);
+      e_l = tt < n ? acc : 0.f;
     }
     // replay the chunk's steps of Eq. 5 with its errors (pre-step values on every right-hand side)
+    float qwinv[KPL];   // q_w^-a: turns Aw back into the w-update coefficient g_w |R_t|^-1/2 x_tk
 #pragma unroll
-    for (int t = 0; t < CH; ++t) {
-      if (t < n) {
-        const float e_ = e[t];
-        const int32_t i = C.i[t];
-        const float gu = g_u * e_, gv = g_v * e_, gc = C.gc[t] * e_;
-        float *urow = a.U + int64_t(i) * F;
+    for (int kk = 0; kk < KPL; ++kk) qwinv[kk] = 1.f;
+#pragma unroll 1
+    for (int t = 0; t < n; ++t) {
+      const float e_ = __shfl_sync(0xffffffffu, e_l, t);
+      const int32_t i = C.i[t];
+      const float gu = g_u * e_, gv = g_v * e_, gc = C.gc[t] * e_;
+      float *urow = a.U + int64_t(i) * F;
 #pragma unroll
-        for (int f = 0; f < FPL; ++f) {
-          const int idx = lane * FPL + f;
-          const float u = uu[t][f];
-          if (idx < F) urow[idx] = fmaf(gu, v[f], fmaf(-gl_u, u, u));
-          v[f] = fmaf(gv, u, fmaf(-gl_v, v[f], v[f]));
-        }
-#pragma unroll
-        for (int kk = 0; kk < KPL; ++kk) {
-          const bool ex = (C.m[t][kk] >> lane) & 1u;
-          const bool valid = lane + 32 * kk < K;
-          const float wn = fmaf(e_, C.gx[t][lane + 32 * kk], fmaf(-gl_w, w[kk], w[kk]));
-          const float cn = fmaf(-gl_c, c[kk], c[kk]) + gc;
-          w[kk] = ex ? wn : w[kk];
-          c[kk] = !ex && valid ? cn : c[kk];
-        }
-        bh = fmaf(-gl_bh, bh, bh) + g_bh * e_;
-        sqf = fmaf(e_, e_, sqf);
+      for (int f = 0; f < FPL; ++f) {
+        const int idx = lane * FPL + f;
+        const float u = C.u[t][idx];
+        if (idx < F) urow[idx] = fmaf(gu, v[f], fmaf(-gl_u, u, u));
+        v[f] = fmaf(gv, u, fmaf(-gl_v, v[f], v[f]));
       }
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const bool ex = (C.m[t][kk] >> lane) & 1u;
+        const bool valid = lane + 32 * kk < K;
+        const float gx = g_w * C.aw[t][lane + 32 * kk] * qwinv[kk];
+        const float wn = fmaf(e_, gx, fmaf(-gl_w, w[kk], w[kk]));
+        const float cn = fmaf(-gl_c, c[kk], c[kk]) + gc;
+        w[kk] = ex ? wn : w[kk];
+        qwinv[kk] = ex ? qwinv[kk] * qwi1 : qwinv[kk];
+        c[kk] = !ex && valid ? cn : c[kk];
+      }
+      bh = fmaf(-gl_bh, bh, bh) + g_bh * e_;
+      sqf = fmaf(e_, e_, sqf);
     }
     // user biases: lane t
     if (lane < n) {
-      float e_l = e[0];
-#pragma unroll
-      for (int t = 1; t < CH; ++t) e_l = lane == t ? e[t] : e_l;
       const float bi = C.b[lane];
       a.b[C.i[lane]] = fmaf(-gl_b, bi, bi) + g_b * e_l;
     }
     // release the chunk's users to the later items of the block (after the
     // whole warp's stores of u_i and b_i)
     __syncwarp();
-    if (lane < n) {
-      const int r = C.rel[lane];
-      st_rel(&sm.cnt[r], C.relv[lane]);
-    }
+    if (lane < n) st_rel(&sm.cnt[C.rel[lane]], C.relv[lane]);
     if (flags & FL_LAST) {
 #pragma unroll
       for (int f = 0; f < FPL; ++f) {
@@ -800,22 +831,20 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
     }
     const int slot = C.slot;
     __syncwarp();
-    if (lane == 0) {
-      if (flags & FL_LAST) {
-        __threadfence_block();   // the block's releases above precede the slot's reuse
-        atomicSub(&ctl->slot_left[slot], 1);
-      }
-      st_rel(&G.freed[buf], pos / NRING + 1);
+    if (lane == 0 && (flags & FL_LAST)) {
+      __threadfence_block();   // the block's releases above precede the slot's reuse
+      atomicSub(&ctl->slot_left[slot], 1);
     }
+    mbar_arrive(&G.empty[buf]);   // every lane's reads of the chunk are done
   }
 }
 
 template <int FPL, int KPL>
-__global__ void __launch_bounds__(32 * MAX_GROUPS * (GP + 1), 1)
+__global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
 k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
-  // carve shared memory: [groups][ctl][qt][cq][cqs][users][cnt]
+  // carve shared memory: [groups][ctl][qt][queue][users][cnt]
   Group<FPL, KPL> *grp = reinterpret_cast<Group<FPL, KPL> *>(smem_raw);
   unsigned char *ptr = smem_raw + sizeof(Group<FPL, KPL>) * ngroups;
   Smem sm;
@@ -823,25 +852,31 @@ k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   ptr += sizeof(CtaCtl);
   sm.qt = reinterpret_cast<float(*)[CH + 1]>(ptr);
   ptr += sizeof(float) * 8 * (CH + 1);
-  sm.cq = reinterpret_cast<int *>(ptr);
-  ptr += sizeof(int) * a.cqn;
+  sm.cq = reinterpret_cast<SegInfo *>(ptr);
+  ptr += sizeof(SegInfo) * a.cqn;
   sm.users = reinterpret_cast<int *>(ptr);
   ptr += sizeof(int) * a.nslots * a.maxu;
   sm.cnt = reinterpret_cast<int *>(ptr);
-  ptr += sizeof(int) * a.nslots * a.maxu;
-  sm.cqs = reinterpret_cast<int8_t *>(ptr);
   // zero the groups (padding columns and unused rows must read as 0) and the control words
   {
     const size_t nz = (sizeof(Group<FPL, KPL>) * ngroups + sizeof(CtaCtl)) / 16;
     float4 *z = reinterpret_cast<float4 *>(smem_raw);
     for (size_t x = threadIdx.x; x < nz; x += blockDim.x) z[x] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  __syncthreads();
+  if (threadIdx.x < ngroups * NRING) {
+    mbar_init(&grp[threadIdx.x / NRING].full[threadIdx.x % NRING], 32);
+    mbar_init(&grp[threadIdx.x / NRING].empty[threadIdx.x % NRING], 32);
+  }
   for (int x = threadIdx.x; x < 8 * (CH + 1); x += blockDim.x)
     sm.qt[x / (CH + 1)][x % (CH + 1)] =
         x < 4 * (CH + 1) ? a.qpow[x / (CH + 1)][x % (CH + 1)] : a.qinv[x / (CH + 1) - 4][x % (CH + 1)];
   __syncthreads();
-  // warps 0..ngroups-1 are the consumers (one per scheduler), the rest producers
-  if (wid < ngroups) {
+  // warps 0..ngroups-1 are the consumers (one per warp scheduler), then the
+  // producers, then the block scheduler
+  if (wid == ngroups * (GP + 1)) {
+    scheduler(a, sm, s);
+  } else if (wid < ngroups) {
     consumer<FPL, KPL>(a, sm, grp[wid]);
   } else if (wid < ngroups * (GP + 1)) {
     const int pw = wid - ngroups;
@@ -870,23 +905,26 @@ __global__ void k_sum_seg_sq(const double *x, int64_t n, double *out) {
 
 template <int FPL, int KPL>
 static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
+  // groups and block slots: as many as fit (the queue holds the segments of every slot's block)
   const size_t gsz = sizeof(Group<FPL, KPL>);
+  const int maxseg = a.cqn;
   auto need = [&](int ng, int ns) {
-    return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + sizeof(int) * size_t(a.cqn) +
-           2 * sizeof(int) * size_t(ns) * a.maxu + size_t(a.cqn) + 16;
+    return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + sizeof(SegInfo) * size_t(ns) * maxseg +
+           2 * sizeof(int) * size_t(ns) * a.maxu;
   };
   int ng = MAX_GROUPS, ns = MAX_SLOTS;
   while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
   while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
   if (need(ng, ns) > size_t(h->smem_optin))
     return set_err(h, LSHMF_EINVAL, "train: %d users or %d segments in one block exceed shared memory; raise P",
-                   a.maxu, a.cqn);
+                   a.maxu, maxseg);
   a.nslots = ns;
+  a.cqn = ns * maxseg;
   const size_t smem = need(ng, ns);
   LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_stratum<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(h->num_sms, a.P);
   for (int s = 0; s < n_strata; ++s)
-    LSHMF_LAUNCH(h, (k_sgd_stratum<FPL, KPL>), grid, 32 * ng * (GP + 1), smem, st, a, s, ng);
+    LSHMF_LAUNCH(h, (k_sgd_stratum<FPL, KPL>), grid, 32 * (ng * (GP + 1) + 1), smem, st, a, s, ng);
   return LSHMF_OK;
 }
 
@@ -918,9 +956,9 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   a.blk_seg = tl.blk_seg.as<int64_t>();
   a.blk_user = tl.blk_user.as<int64_t>();
   a.order = tl.blk_order.as<int32_t>();
+  a.next_blk = tl.next_blk.as<int32_t>();
   a.users = tl.users.as<int32_t>();
   a.bh0n = tl.bh0n.as<float>();
-  a.next_blk = tl.next_blk.as<int32_t>();
   a.seg_sq = tl.seg_sq.as<double>();
   a.U = p->U; a.V = p->V; a.b = p->b; a.bh = p->bh; a.W = p->W; a.C = p->C;
   a.mu = float(p->mu);
@@ -942,7 +980,7 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
     }
   }
   a.F = c.F; a.K = c.K; a.P = c.P; a.mw = tl.mask_words; a.maxu = std::max(1, tl.max_users_per_block);
-  a.cqn = std::max(1, tl.max_segs_per_block);
+  a.cqn = std::max(1, tl.max_segs_per_block);   // segments per block; the queue size is set at launch
   a.nslots = 1;
   a.want_sq = h_sq != nullptr;
   a.err = h->d_err;
