@@ -58,6 +58,7 @@ def _load():
         "oracle_topk_rows": [I64, I32, I32, P, I64, P, P],
         "oracle_rating_step": [I32, I32, D, D, P, P, P, P, P, P, P, P, P, P, P],
         "oracle_train": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I32, I32, I32, P],
+        "oracle_ingest_sgd": [CP, I64, I64, I64, P, P, P, I64, P, P, P, P, D, P, P, P, P, P, P, I32],
         "oracle_predict": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P],
         "oracle_rmse": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P, P],
         "oracle_loss": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, P],
@@ -222,6 +223,15 @@ def train(cfg, ti, tj, tr, nbr, mu, params: Params, epoch, s_begin=0, s_end=None
     _check(_load().oracle_train(ctypes.byref(cfg), len(ti), _p(ti), _p(tj), _p(tr), _p(nbr), mu,
                                 *params.ptrs(), epoch, s_begin, s_end, ctypes.byref(se)), "train")
     return se.value
+
+
+def ingest_sgd(cfg, M_old, N_old, oi, oj, orr, ni, nj, nr, nbr, mu, params: Params, epochs):
+    """Local SGD of the online update (Sec. 4.3, Alg. 4 lines 10-15), in place.
+    cfg holds the sizes after the update; users >= M_old and items >= N_old are new."""
+    oi, oj, orr = _c(oi, np.int32), _c(oj, np.int32), _c(orr, np.uint8)
+    ni, nj, nr, nbr = _c(ni, np.int32), _c(nj, np.int32), _c(nr, np.uint8), _c(nbr, np.int32)
+    _check(_load().oracle_ingest_sgd(ctypes.byref(cfg), M_old, N_old, len(oi), _p(oi), _p(oj), _p(orr), len(ni),
+                                     _p(ni), _p(nj), _p(nr), _p(nbr), mu, *params.ptrs(), epochs), "ingest_sgd")
 
 
 def predict(cfg, ti, tj, tr, nbr, mu, params: Params, qi, qj):

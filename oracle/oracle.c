@@ -14,6 +14,8 @@
  *   oracle_train                                Sec. 4.2, Alg. 3 with the
  *                                               stratified P x P block schedule
  *   oracle_predict / oracle_rmse / oracle_loss  Eq. (1), Eq. (6), Eq. (2)
+ *   oracle_ingest_sgd                           Sec. 4.3, Alg. 4 local SGD of the
+ *                                               online update
  *
  * Readings of passages the paper leaves open (each is also listed in the
  * design notes):
@@ -464,6 +466,101 @@ int oracle_train(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int3
   }
   if (sq_err) *sq_err = se;
   free(bptr); free(bfill); free(rat); free(bh0); free_user_lists(&ul);
+  return ORC_OK;
+}
+
+/* Sec. 4.3, Alg. 4 (lines 10-15): the local SGD of the online update.
+ * Users [M_old, c->M) and items [N_old, c->N) are new; c->M, c->N are the
+ * sizes after the update.  The old ratings are the training set of the model
+ * before the update, the new ratings those of the increment (each has a new
+ * user or a new item).  nbr holds the rows of all items (the kept rows of old
+ * items, the searched rows of new items).  R(i) is the user's items over old
+ * and new ratings.  For loop t = 0..epochs-1 (learning rate of Eq. (7) at t):
+ *   lines 10-12: new users in ascending order, each over its new ratings of
+ *     OLD items in item order: Eq. (1), then the b and u updates of Eq. (5);
+ *     item parameters stay as they are;
+ *   lines 13-15: new items in ascending order, each over its ratings (every
+ *     rating of a new item is new) in user order: Eq. (1) with neighbour
+ *     baselines from the bhat of the pass start, then the bhat, v, w, c
+ *     updates of Eq. (5); user parameters stay as they are.
+ * The updates are those of oracle_rating_step; the side that stays fixed is
+ * passed as a scratch copy whose update is discarded. */
+int oracle_ingest_sgd(const oracle_cfg *c, int64_t M_old, int64_t N_old, int64_t n_old, const int32_t *oi,
+                      const int32_t *oj, const uint8_t *or_, int64_t n_new, const int32_t *ni,
+                      const int32_t *nj, const uint8_t *nr, const int32_t *nbr, double mu, double *U, double *V,
+                      double *b, double *bh, double *W, double *C, int32_t epochs) {
+  const int64_t M = c->M, N = c->N;
+  const int32_t F = c->F, K = c->K;
+  if (F <= 0 || K <= 0 || F > 1024 || K > 1024 || M_old < 0 || N_old < 0 || M_old > M || N_old > N)
+    return ORC_EINVAL;
+  if (validate(M_old, N_old, n_old, oi, oj) != ORC_OK || validate(M, N, n_new, ni, nj) != ORC_OK) return ORC_EINVAL;
+  for (int64_t p = 0; p < n_new; ++p)
+    if (ni[p] < M_old && nj[p] < N_old) return ORC_EINVAL;   /* an old pair is not part of an increment */
+  /* R(i) over old and new ratings */
+  int64_t n_all = n_old + n_new;
+  int32_t *ai = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_all > 0 ? n_all : 1));
+  int32_t *aj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_all > 0 ? n_all : 1));
+  uint8_t *ar = (uint8_t *)malloc((size_t)(n_all > 0 ? n_all : 1));
+  rat_t *byu = (rat_t *)malloc(sizeof(rat_t) * (size_t)(n_new > 0 ? n_new : 1));
+  rat_t *byi = (rat_t *)malloc(sizeof(rat_t) * (size_t)(n_new > 0 ? n_new : 1));
+  double *bh0 = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!ai || !aj || !ar || !byu || !byi || !bh0) {
+    free(ai); free(aj); free(ar); free(byu); free(byi); free(bh0);
+    return ORC_ENOMEM;
+  }
+  memcpy(ai, oi, sizeof(int32_t) * (size_t)n_old);
+  memcpy(aj, oj, sizeof(int32_t) * (size_t)n_old);
+  memcpy(ar, or_, (size_t)n_old);
+  memcpy(ai + n_old, ni, sizeof(int32_t) * (size_t)n_new);
+  memcpy(aj + n_old, nj, sizeof(int32_t) * (size_t)n_new);
+  memcpy(ar + n_old, nr, (size_t)n_new);
+  user_lists ul;
+  if (build_user_lists(M, n_all, ai, aj, ar, &ul) != ORC_OK) {
+    free(ai); free(aj); free(ar); free(byu); free(byi); free(bh0);
+    return ORC_ENOMEM;
+  }
+  /* new ratings by (user, item) -- cmp_rat orders by its first field, then its second --
+   * and by (item, user) */
+  for (int64_t p = 0; p < n_new; ++p) {
+    rat_t x = {ni[p], nj[p], nr[p]};   /* fields (j, i) hold (user, item) here */
+    rat_t y = {nj[p], ni[p], nr[p]};
+    byu[p] = x;
+    byi[p] = y;
+  }
+  qsort(byu, (size_t)n_new, sizeof(rat_t), cmp_rat);
+  qsort(byi, (size_t)n_new, sizeof(rat_t), cmp_rat);
+  uint8_t expl[1024];
+  double rnb[1024], bnb[1024], sv[1024], sw[1024], sc[1024], su[1024];
+  for (int32_t t = 0; t < epochs; ++t) {
+    double gam[6], lam[6];
+    double tfac = 1.0 + c->beta * pow((double)t, 1.5);   /* Eq. (7) */
+    for (int g = 0; g < 6; ++g) { gam[g] = c->alpha[g] / tfac; lam[g] = c->lambda[g]; }
+    /* lines 10-12: new users over old items; items stay fixed */
+    for (int64_t p = 0; p < n_new; ++p) {
+      int64_t i = byu[p].j, j = byu[p].i;
+      if (i < M_old || j >= N_old) continue;
+      neighbours_of(c, &ul, i, j, nbr, bh, expl, rnb, bnb);
+      memcpy(sv, V + j * F, sizeof(double) * (size_t)F);
+      memcpy(sw, W + j * K, sizeof(double) * (size_t)K);
+      memcpy(sc, C + j * K, sizeof(double) * (size_t)K);
+      double sbh = bh[j];
+      oracle_rating_step(F, K, (double)byu[p].r / c->rating_scale, mu, U + i * F, sv, b + i, &sbh, sw, sc, expl,
+                         rnb, bnb, gam, lam);
+    }
+    /* lines 13-15: new items over all their raters; users stay fixed */
+    memcpy(bh0, bh, sizeof(double) * (size_t)N);
+    for (int64_t p = 0; p < n_new; ++p) {
+      int64_t j = byi[p].j, i = byi[p].i;
+      if (j < N_old) continue;
+      neighbours_of(c, &ul, i, j, nbr, bh0, expl, rnb, bnb);
+      memcpy(su, U + i * F, sizeof(double) * (size_t)F);
+      double sb = b[i];
+      oracle_rating_step(F, K, (double)byi[p].r / c->rating_scale, mu, su, V + j * F, &sb, bh + j, W + j * K,
+                         C + j * K, expl, rnb, bnb, gam, lam);
+    }
+  }
+  free_user_lists(&ul);
+  free(ai); free(aj); free(ar); free(byu); free(byi); free(bh0);
   return ORC_OK;
 }
 
