@@ -14,6 +14,7 @@
  *   lshmf_train_epoch       one stratified SGD epoch of Eq. (1) / Eq. (5)
  *                           with the learning rate of Eq. (7) (Alg. 3)
  *   lshmf_predict/_rmse     Eq. (1) on query pairs, Eq. (6)
+ *   lshmf_ingest            the online update of Sec. 4.3 (Alg. 4)
  *
  * Conventions shared by every entry point:
  *  - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
@@ -158,6 +159,37 @@ lshmf_status lshmf_train_epoch(lshmf_handle *h, const lshmf_params *p, int32_t e
  * the bhat snapshot is taken when the call starts). */
 lshmf_status lshmf_train_strata(lshmf_handle *h, const lshmf_params *p, int32_t epoch,
                                 int32_t n_strata, double *h_sq_err, void *stream);
+
+/* Online update (Sec. 4.3, Alg. 4).  The handle's model covers M users x N
+ * items (its configuration); the increment brings users [M, M + M_new),
+ * items [N, N + N_new) and n ratings (d_i, d_j, d_r: int32, int32, uint8 on
+ * the device), each of which has a new user or a new item (an old user with
+ * an old item, an index out of range or a repeated pair: EINVAL).
+ *  - Alg. 4 lines 1-6: the integer pre-sign sums of Eq. (3) that
+ *    lshmf_build_neighbours kept for every item receive Psi(r) (2 H_i - 1) of
+ *    each new rating; keys of all items follow from the sums (Upsilon), so they
+ *    equal a neighbour build over all ratings, bit for bit.  d_H: the hash
+ *    bits of all M + M_new users (the first M rows as given to the build).
+ *  - lines 7-9: the top-K rows (Alg. 1 rule) of the new items over all
+ *    N + N_new items are written to d_nbr[N .. N + N_new) (d_nbr: int32
+ *    [(N + N_new) x K]; rows of old items are kept as the caller holds them).
+ *    d_sig (NULL allowed): receives the keys of all items, uint32 [L x (N + N_new)].
+ *  - lines 10-15, local_epochs times (learning rate of Eq. 7 at the loop index
+ *    from 0): each new user's new ratings of old items in item order (Eq. 1, then
+ *    the b and u updates of Eq. 5; items fixed), then each new item's ratings in
+ *    user order (Eq. 1 with neighbour baselines from bhat at the start of the
+ *    pass, then the bhat, v, w, c updates; users fixed).  R(i) is the user's
+ *    items over the prepared training set and the increment.
+ * p: parameter arrays sized for M + M_new users and N + N_new items, rows of the
+ * new users and items initialised by the caller; p->mu is the model's mean
+ * (kept).  Requires lshmf_build_neighbours and lshmf_prepare_training of the
+ * current model.  Afterwards the handle describes M + M_new users and N + N_new
+ * items and its training layout is dropped: call lshmf_prepare_training with
+ * all ratings before training or predicting again.  Synchronous. */
+lshmf_status lshmf_ingest(lshmf_handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
+                          const int32_t *d_j, const uint8_t *d_r, int64_t n, const uint64_t *d_H,
+                          int32_t *d_nbr, uint32_t *d_sig, const lshmf_params *p, int32_t local_epochs,
+                          void *stream);
 
 /* Sizes of the prepared training layout (for memory planning and for the
  * algorithmic byte count of an epoch: every rating reads its user slot,

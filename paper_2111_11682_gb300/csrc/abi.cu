@@ -13,6 +13,9 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
                           cudaStream_t st);
 lshmf_status predict(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, int64_t n, float *out,
                      cudaStream_t st);
+lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i, const int32_t *d_j,
+                    const uint8_t *d_r, int64_t n, const uint64_t *d_H, int32_t *d_nbr, uint32_t *d_sig,
+                    const lshmf_params *p, int32_t epochs, cudaStream_t st);
 lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, const uint8_t *qr,
                   int64_t n, double *h_rmse, cudaStream_t st);
 
@@ -85,6 +88,8 @@ void lshmf_destroy(lshmf_handle *hh) {
   for (auto &b : h->prep) release(b);
   release(h->red_part);
   release(h->aux);
+  release(h->lsh.sums);
+  for (auto &b : h->ing) release(b);
   TrainLayout &t = h->tl;
   DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                     &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
@@ -147,6 +152,16 @@ lshmf_status lshmf_train_strata(lshmf_handle *hh, const lshmf_params *p, int32_t
   return train_strata(&hh->h, p, epoch, n_strata, h_sq_err, S(stream));
 }
 
+lshmf_status lshmf_ingest(lshmf_handle *hh, int64_t M_new, int64_t N_new, const int32_t *d_i, const int32_t *d_j,
+                          const uint8_t *d_r, int64_t n, const uint64_t *d_H, int32_t *d_nbr, uint32_t *d_sig,
+                          const lshmf_params *p, int32_t local_epochs, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (M_new < 0 || N_new < 0) return set_err(h, LSHMF_EINVAL, "ingest: negative new user/item count");
+  if (h->cfg.K >= h->cfg.N + N_new) return set_err(h, LSHMF_EINVAL, "ingest: K must be < N");
+  return ingest(h, M_new, N_new, d_i, d_j, d_r, n, d_H, d_nbr, d_sig, p, local_epochs, S(stream));
+}
+
 lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out) {
   if (!hh || !out) return LSHMF_EINVAL;
   const Handle *h = &hh->h;
@@ -165,7 +180,8 @@ lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out
                           &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
                           &t.seg_ck, &t.ck_roff, &t.next_blk};
   for (const DevBuf *b : bufs) bytes += b->bytes;
-  out->device_bytes = bytes + h->red_part.bytes;
+  for (const auto &b : h->ing) bytes += b.bytes;
+  out->device_bytes = bytes + h->red_part.bytes + h->lsh.sums.bytes + h->aux.bytes;
   return LSHMF_OK;
 }
 

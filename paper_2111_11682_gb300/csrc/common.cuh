@@ -68,6 +68,16 @@ struct TrainLayout {
   int64_t nchunks = 0;
 };
 
+// simLSH state kept by lshmf_build_neighbours for the online update (Sec. 4.3):
+// the exact integer pre-sign sums of every item, N x 64W (W = padded 64-bit
+// words of hash bits; bit b of item j at j * 64W + b).
+struct LshState {
+  bool ready = false;
+  int W = 0;
+  int64_t N = 0;
+  DevBuf sums;      // int64 [N x 64W]
+};
+
 constexpr int PREP_BUFS = 25;
 
 struct Handle {
@@ -83,6 +93,8 @@ struct Handle {
   DevBuf red_part;              // per-CTA partial sums of reductions
   DevBuf aux;                   // top-K overflow tables
   TrainLayout tl;
+  LshState lsh;
+  DevBuf ing[8];                // online update scratch
 };
 
 inline lshmf_status cuda_status(Handle *h, cudaError_t e, const char *what) {
@@ -142,6 +154,11 @@ constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;
 // are clobbered.  n < 2^31.
 lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, uint64_t *keys_out,
                               uint32_t *vals_out, int64_t n, int nbits, cudaStream_t st);
+// ---- simLSH stages shared with the online update (simlsh.cu) ----
+// Top-K rows of all N items from keys sig (L x N) into nbr (N x K).
+lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *nbr, cudaStream_t st);
+// Keys (L x N) from pre-sign sums (N x 64W).
+lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, uint32_t *sig, cudaStream_t st);
 // Exclusive scan of n int64 values (out may alias in); out[n] = total.
 lshmf_status exclusive_scan_i64(Handle *h, const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
 // Synchronously checks 0 <= x[k] < hi for k < n (EINVAL otherwise).

@@ -1,0 +1,391 @@
+// Online update of LSH-MF (Sec. 4.3, Alg. 4) on sm_103a.
+//
+// The model was built for M users x N items; an increment brings users
+// [M, M + M_new), items [N, N + N_new) and n ratings, each with a new user or
+// a new item.
+//   signatures (Alg. 4 lines 1-6): the kept integer pre-sign sums of every
+//     item (Eq. 3 before Upsilon, kept by the neighbour build) receive
+//     Psi(r) (2 H_i - 1) of every new rating by integer atomics (exact, any
+//     order); keys of all items are re-derived from the sums.
+//   neighbours (lines 7-9): top-K rows of the new items over all items, from
+//     those keys; old items keep their rows.
+//   local SGD (lines 10-15), for each of `local_epochs` loops t (Eq. 7 at t):
+//     one warp per new user runs the user's new ratings of old items in item
+//     order, Eq. (1) then the b and u updates of Eq. (5), items fixed; then one
+//     warp per new item runs its raters in user order, Eq. (1) with neighbour
+//     baselines from the bhat of the pass start, then the bhat, v, w, c
+//     updates, users fixed.  R(i) is the user's items over the old training
+//     set and the increment.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace lshmf {
+
+// Sort keys of the increment and validation: key_u = i * Nt + j, key_i = j * Mt + i.
+__global__ void k_ing_keys(const int32_t *ii, const int32_t *jj, int64_t n, int64_t M, int64_t N, int64_t Mt,
+                           int64_t Nt, uint64_t *ku, uint64_t *ki, uint32_t *vu, uint32_t *vi, int32_t *err) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = ii[p], j = jj[p];
+    const bool bad = i < 0 || i >= Mt || j < 0 || j >= Nt || (i < M && j < N);
+    if (bad) atomicOr(err, DERR_INDEX);
+    const int64_t ci = bad ? 0 : i, cj = bad ? 0 : j;
+    ku[p] = uint64_t(ci) * uint64_t(Nt) + uint64_t(cj);
+    ki[p] = uint64_t(cj) * uint64_t(Mt) + uint64_t(ci);
+    vu[p] = uint32_t(p);
+    vi[p] = uint32_t(p);
+  }
+}
+
+// Gathers a sorted order: other index (item for the user order, user for the
+// item order) and rating; flags duplicate pairs.
+__global__ void k_ing_emit(const uint64_t *ks, const uint32_t *vs, int64_t n, uint64_t div, const uint8_t *r,
+                           int32_t *other, uint8_t *rr, int32_t *err) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    other[x] = int32_t(ks[x] % div);
+    rr[x] = r[vs[x]];
+    if (x > 0 && ks[x] == ks[x - 1]) atomicOr(err, DERR_DUP);
+  }
+}
+
+// ptr[g] = first x with ks[x] / div >= g, for g in [0, G]; ptr[G] = n.
+__global__ void k_ing_ptr(const uint64_t *ks, int64_t n, uint64_t div, int64_t G, int64_t *ptr) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x <= n; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t lo = x == 0 ? 0 : int64_t(ks[x - 1] / div) + 1;
+    const int64_t hi = x == n ? G : int64_t(ks[x] / div);
+    for (int64_t g = lo; g <= hi; ++g) ptr[g] = x;
+  }
+}
+
+// Alg. 4 lines 1-6: sums[j][b] += Psi(r) (2 H_i[b] - 1), one warp per rating.
+__global__ void k_ing_sums(const int32_t *ii, const int32_t *jj, const uint8_t *r, int64_t n, const uint64_t *H,
+                           int hstride, int W, int psi_pow, int64_t *sums) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < n;
+       p += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int64_t i = ii[p], j = jj[p];
+    int64_t ps = 1;
+    for (int q = 0; q < psi_pow; ++q) ps *= int64_t(r[p]);
+    for (int w = 0; w < W; ++w) {
+      const uint64_t hw = w < hstride ? H[i * hstride + w] : 0ull;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int64_t v = ((hw >> (32 * half + lane)) & 1ull) ? ps : -ps;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sums[j * (64 * W) + 64 * w + 32 * half + lane]),
+                  (unsigned long long)v);
+      }
+    }
+  }
+}
+
+__global__ void k_ing_copy_rows(const int32_t *src, int64_t first, int64_t nrows, int K, int32_t *dst) {
+  const int64_t n = nrows * K;
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
+    dst[first * K + x] = src[first * K + x];
+}
+
+// Rating of item q in the sorted items[lo, hi) (with ratings rs), or -1.
+__device__ __forceinline__ int find_in(const int32_t *items, const uint8_t *rs, int64_t lo, int64_t hi, int32_t q) {
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if (items[m] < q) lo = m + 1;
+    else hi = m;
+  }
+  return (lo < end && items[lo] == q) ? int(rs[lo]) : -1;
+}
+
+struct IngArgs {
+  // increment by user: items and ratings, ptr over Mt + 1
+  const int64_t *nu_ptr;
+  const int32_t *nu_j;
+  const uint8_t *nu_r;
+  // increment by item: users and ratings, ptr over Nt + 1
+  const int64_t *ni_ptr;
+  const int32_t *ni_i;
+  const uint8_t *ni_r;
+  // training set of the model before the update, by user (items ascending)
+  const int64_t *old_ptr;
+  const int32_t *old_j;
+  const uint8_t *old_r;
+  const int32_t *nbr;    // Nt x K
+  const float *bh0;      // bhat at the start of the item pass
+  float *U, *V, *b, *bh, *W, *C;
+  float mu, inv_scale;
+  float gam[6], lam[6];
+  int64_t M, N, Mt, Nt;
+  int F, K;
+};
+
+// Warp sum of three values.
+__device__ __forceinline__ void warp_sum3(float &x, float &y, float &z) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+  }
+}
+
+// Alg. 4 lines 10-12: one warp per new user; items fixed.
+template <int FPL, int KPL>
+__global__ void k_ing_users(const IngArgs a) {
+  const int lane = threadIdx.x & 31, F = a.F, K = a.K;
+  const float g_b = a.gam[0], g_u = a.gam[2], l_b = a.lam[0], l_u = a.lam[2];
+  for (int64_t i = a.M + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); i < a.Mt;
+       i += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int64_t lo = a.nu_ptr[i], hi = a.nu_ptr[i + 1];
+    float u[FPL];
+#pragma unroll
+    for (int f = 0; f < FPL; ++f) u[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
+    float bi = a.b[i];
+    for (int64_t p = lo; p < hi; ++p) {
+      const int32_t j = a.nu_j[p];
+      if (j >= a.N) continue;
+      const float r = float(a.nu_r[p]) * a.inv_scale;
+      float v[FPL];
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) v[f] = lane * FPL + f < F ? a.V[int64_t(j) * F + lane * FPL + f] : 0.f;
+      float sxw = 0.f, sc = 0.f, dot = 0.f;
+      int nR = 0, nV = 0;
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const int k = lane + 32 * kk;
+        const bool valid = k < K;
+        int rq = -1;
+        float wk = 0.f, ck = 0.f, bq = 0.f;
+        if (valid) {
+          const int32_t q = a.nbr[int64_t(j) * K + k];
+          rq = find_in(a.nu_j, a.nu_r, lo, hi, q);
+          wk = a.W[int64_t(j) * K + k];
+          ck = a.C[int64_t(j) * K + k];
+          bq = a.bh[q];
+        }
+        const bool ex = rq >= 0;
+        const float x = ex ? float(rq) * a.inv_scale - (a.mu + bi + bq) : 0.f;
+        sxw = fmaf(x, wk, sxw);
+        sc += (valid && !ex) ? ck : 0.f;
+        nR += __popc(__ballot_sync(0xffffffffu, ex));
+        nV += __popc(__ballot_sync(0xffffffffu, valid));
+      }
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) dot = fmaf(u[f], v[f], dot);
+      warp_sum3(sxw, sc, dot);
+      const int nN = nV - nR;
+      const float rhat = a.mu + bi + a.bh[j] + (nR > 0 ? sxw * rsqrtf(float(nR)) : 0.f) +
+                         (nN > 0 ? sc * rsqrtf(float(nN)) : 0.f) + dot;
+      const float e = r - rhat;
+      bi = bi + g_b * (e - l_b * bi);
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) u[f] = u[f] + g_u * (e * v[f] - l_u * u[f]);
+    }
+#pragma unroll
+    for (int f = 0; f < FPL; ++f)
+      if (lane * FPL + f < F) a.U[i * F + lane * FPL + f] = u[f];
+    if (lane == 0) a.b[i] = bi;
+  }
+}
+
+// Alg. 4 lines 13-15: one warp per new item; users fixed.
+template <int FPL, int KPL>
+__global__ void k_ing_items(const IngArgs a) {
+  const int lane = threadIdx.x & 31, F = a.F, K = a.K;
+  const float g_bh = a.gam[1], g_v = a.gam[3], g_w = a.gam[4], g_c = a.gam[5];
+  const float l_bh = a.lam[1], l_v = a.lam[3], l_w = a.lam[4], l_c = a.lam[5];
+  for (int64_t j = a.N + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); j < a.Nt;
+       j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    float v[FPL], w[KPL], c[KPL];
+    int32_t q[KPL];
+#pragma unroll
+    for (int f = 0; f < FPL; ++f) v[f] = lane * FPL + f < F ? a.V[j * F + lane * FPL + f] : 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KPL; ++kk) {
+      const int k = lane + 32 * kk;
+      w[kk] = k < K ? a.W[j * K + k] : 0.f;
+      c[kk] = k < K ? a.C[j * K + k] : 0.f;
+      q[kk] = k < K ? a.nbr[j * K + k] : 0;
+    }
+    float bhj = a.bh[j];
+    for (int64_t p = a.ni_ptr[j]; p < a.ni_ptr[j + 1]; ++p) {
+      const int64_t i = a.ni_i[p];
+      const float r = float(a.ni_r[p]) * a.inv_scale;
+      const float bi = a.b[i];
+      float u[FPL];
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) u[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
+      const int64_t nlo = a.nu_ptr[i], nhi = a.nu_ptr[i + 1];
+      const int64_t olo = i < a.M ? a.old_ptr[i] : 0, ohi = i < a.M ? a.old_ptr[i + 1] : 0;
+      float xk[KPL];
+      bool exk[KPL];
+      float sxw = 0.f, sc = 0.f, dot = 0.f;
+      int nR = 0, nV = 0;
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const int k = lane + 32 * kk;
+        const bool valid = k < K;
+        int rq = -1;
+        if (valid) {
+          rq = find_in(a.old_j, a.old_r, olo, ohi, q[kk]);
+          if (rq < 0) rq = find_in(a.nu_j, a.nu_r, nlo, nhi, q[kk]);
+        }
+        const bool ex = rq >= 0;
+        const float x = ex ? float(rq) * a.inv_scale - (a.mu + bi + a.bh0[q[kk]]) : 0.f;
+        xk[kk] = x;
+        exk[kk] = ex;
+        sxw = fmaf(x, w[kk], sxw);
+        sc += (valid && !ex) ? c[kk] : 0.f;
+        nR += __popc(__ballot_sync(0xffffffffu, ex));
+        nV += __popc(__ballot_sync(0xffffffffu, valid));
+      }
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) dot = fmaf(u[f], v[f], dot);
+      warp_sum3(sxw, sc, dot);
+      const int nN = nV - nR;
+      const float sR = nR > 0 ? rsqrtf(float(nR)) : 0.f, sN = nN > 0 ? rsqrtf(float(nN)) : 0.f;
+      const float rhat = a.mu + bi + bhj + sxw * sR + sc * sN + dot;
+      const float e = r - rhat;
+      bhj = bhj + g_bh * (e - l_bh * bhj);
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) v[f] = v[f] + g_v * (e * u[f] - l_v * v[f]);
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const bool valid = lane + 32 * kk < K;
+        if (exk[kk]) w[kk] = w[kk] + g_w * (sR * e * xk[kk] - l_w * w[kk]);
+        else if (valid) c[kk] = c[kk] + g_c * (sN * e - l_c * c[kk]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < FPL; ++f)
+      if (lane * FPL + f < F) a.V[j * F + lane * FPL + f] = v[f];
+#pragma unroll
+    for (int kk = 0; kk < KPL; ++kk) {
+      const int k = lane + 32 * kk;
+      if (k < K) {
+        a.W[j * K + k] = w[kk];
+        a.C[j * K + k] = c[kk];
+      }
+    }
+    if (lane == 0) a.bh[j] = bhj;
+  }
+}
+
+template <int FPL, int KPL>
+static lshmf_status run_local_sgd(Handle *h, IngArgs a, int epochs, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  const int64_t nu = a.Mt - a.M, ni = a.Nt - a.N;
+  const unsigned gu = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nu, 8), 16L * h->num_sms));
+  const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ni, 8), 16L * h->num_sms));
+  for (int t = 0; t < epochs; ++t) {
+    const double tfac = 1.0 + double(c.beta) * std::pow(double(t), 1.5);   // Eq. (7)
+    for (int g = 0; g < 6; ++g) {
+      a.gam[g] = float(double(c.alpha[g]) / tfac);
+      a.lam[g] = c.lambda[g];
+    }
+    if (nu > 0) LSHMF_LAUNCH(h, (k_ing_users<FPL, KPL>), gu, 256, 0, st, a);
+    LSHMF_CUDA(h, cudaMemcpyAsync(const_cast<float *>(a.bh0), a.bh, a.Nt * 4, cudaMemcpyDeviceToDevice, st));
+    if (ni > 0) LSHMF_LAUNCH(h, (k_ing_items<FPL, KPL>), gi, 256, 0, st, a);
+  }
+  return LSHMF_OK;
+}
+
+lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i, const int32_t *d_j,
+                    const uint8_t *d_r, int64_t n, const uint64_t *d_H, int32_t *d_nbr, uint32_t *d_sig,
+                    const lshmf_params *p, int32_t epochs, cudaStream_t st) {
+  lshmf_config &c = h->cfg;
+  LshState &S = h->lsh;
+  TrainLayout &tl = h->tl;
+  const int64_t M = c.M, N = c.N, Mt = M + M_new, Nt = N + N_new;
+  if (!S.ready || S.N != N) return set_err(h, LSHMF_ESTATE, "ingest: lshmf_build_neighbours has not run for this model");
+  if (!tl.ready) return set_err(h, LSHMF_ESTATE, "ingest: lshmf_prepare_training has not run for this model");
+  if (M_new < 0 || N_new < 0 || Mt >= (int64_t(1) << 31) || Nt >= (int64_t(1) << 31))
+    return set_err(h, LSHMF_EINVAL, "ingest: bad new user/item counts");
+  if (n < 0 || n >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "ingest: n out of range");
+  if (epochs < 0) return set_err(h, LSHMF_EINVAL, "ingest: local_epochs < 0");
+  if (!d_H || !d_nbr || (n > 0 && (!d_i || !d_j || !d_r))) return set_err(h, LSHMF_EINVAL, "ingest: null pointer");
+  if (!p || !p->U || !p->V || !p->b || !p->bh || !p->W || !p->C)
+    return set_err(h, LSHMF_EINVAL, "ingest: null parameter pointer");
+  const int W = S.W;
+  const int64_t nn = std::max<int64_t>(n, 1);
+  // scratch: [0] sums (Nt x 64W), [1] user keys, [2] item keys, [3] sort values and sorted values,
+  // [4] user order (items, ratings, ptr), [5] item order (users, ratings, ptr), [6] all rows, [7] bh0
+  DevBuf *B = h->ing;
+  LSHMF_TRY(ensure(h, B[0], sizeof(int64_t) * 64 * W * Nt + 64, "ingest sums"));
+  LSHMF_TRY(ensure(h, B[1], 2 * sizeof(uint64_t) * nn + 64, "ingest user keys"));
+  LSHMF_TRY(ensure(h, B[2], 2 * sizeof(uint64_t) * nn + 64, "ingest item keys"));
+  LSHMF_TRY(ensure(h, B[3], 4 * sizeof(uint32_t) * nn + 64, "ingest sort values"));
+  LSHMF_TRY(ensure(h, B[4], sizeof(int64_t) * (Mt + 1) + 5 * nn + 128, "ingest user order"));
+  LSHMF_TRY(ensure(h, B[5], sizeof(int64_t) * (Nt + 1) + 5 * nn + 128, "ingest item order"));
+  LSHMF_TRY(ensure(h, B[6], sizeof(int32_t) * Nt * c.K + 64, "ingest rows"));
+  LSHMF_TRY(ensure(h, B[7], sizeof(float) * Nt + 64, "ingest bhat snapshot"));
+  uint64_t *ku = B[1].as<uint64_t>(), *kus = ku + nn, *ki = B[2].as<uint64_t>(), *kis = ki + nn;
+  uint32_t *vu = B[3].as<uint32_t>(), *vus = vu + nn, *vi = vus + nn, *vis = vi + nn;
+  int64_t *nu_ptr = B[4].as<int64_t>();
+  int32_t *nu_j = reinterpret_cast<int32_t *>(nu_ptr + Mt + 1);
+  uint8_t *nu_r = reinterpret_cast<uint8_t *>(nu_j + nn);
+  int64_t *ni_ptr = B[5].as<int64_t>();
+  int32_t *ni_i = reinterpret_cast<int32_t *>(ni_ptr + Nt + 1);
+  uint8_t *ni_r = reinterpret_cast<uint8_t *>(ni_i + nn);
+  LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nn, 256), 16L * h->num_sms));
+  // validation and the two orders of the increment
+  if (n > 0) {
+    LSHMF_LAUNCH(h, k_ing_keys, g, 256, 0, st, d_i, d_j, n, M, N, Mt, Nt, ku, ki, vu, vi, h->d_err);
+    const int kb = bits_for(Mt) + bits_for(Nt);
+    LSHMF_TRY(radix_sort_pairs(h, ku, vu, kus, vus, n, kb, st));
+    LSHMF_TRY(radix_sort_pairs(h, ki, vi, kis, vis, n, kb, st));
+    LSHMF_LAUNCH(h, k_ing_emit, g, 256, 0, st, kus, vus, n, uint64_t(Nt), d_r, nu_j, nu_r, h->d_err);
+    LSHMF_LAUNCH(h, k_ing_emit, g, 256, 0, st, kis, vis, n, uint64_t(Mt), d_r, ni_i, ni_r, h->d_err);
+  }
+  LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kus, n, uint64_t(Nt), Mt, nu_ptr);
+  LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kis, n, uint64_t(Mt), Nt, ni_ptr);
+  LSHMF_TRY(check_device_flag(h, st, "ingest (increment: index out of range, an old user-item pair, or a duplicate)"));
+  // Alg. 4 lines 1-6: sums of the enlarged item set, then keys of all items
+  int64_t *sums = B[0].as<int64_t>();
+  LSHMF_CUDA(h, cudaMemcpyAsync(sums, S.sums.p, sizeof(int64_t) * 64 * W * N, cudaMemcpyDeviceToDevice, st));
+  LSHMF_CUDA(h, cudaMemsetAsync(sums + 64 * W * N, 0, sizeof(int64_t) * 64 * W * (Nt - N), st));
+  if (n > 0) {
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), 16L * h->num_sms));
+    LSHMF_LAUNCH(h, k_ing_sums, gs, 256, 0, st, d_i, d_j, d_r, n, d_H, (c.L * c.bits + 63) / 64, W, c.psi_pow,
+                 sums);
+  }
+  // the handle now describes the enlarged model
+  c.M = Mt;
+  c.N = Nt;
+  std::swap(S.sums, B[0]);
+  S.N = Nt;
+  sums = S.sums.as<int64_t>();
+  LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * Nt + 16, "signatures"));
+  uint32_t *sig = h->tmp[0].as<uint32_t>();
+  LSHMF_TRY(keys_from_sums(h, sums, W, Nt, sig, st));
+  if (d_sig) LSHMF_CUDA(h, cudaMemcpyAsync(d_sig, sig, sizeof(uint32_t) * c.L * Nt, cudaMemcpyDeviceToDevice, st));
+  // lines 7-9: rows of the new items over all items; old rows are kept
+  int32_t *rows = B[6].as<int32_t>();
+  LSHMF_TRY(topk_from_sig(h, sig, Nt, rows, st));
+  if (N_new > 0)
+    LSHMF_LAUNCH(h, k_ing_copy_rows, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N_new * c.K, 256),
+                                                                                     16L * h->num_sms)),
+                 256, 0, st, rows, N, N_new, c.K, d_nbr);
+  // lines 10-15: local SGD
+  IngArgs a;
+  a.nu_ptr = nu_ptr; a.nu_j = nu_j; a.nu_r = nu_r;
+  a.ni_ptr = ni_ptr; a.ni_i = ni_i; a.ni_r = ni_r;
+  a.old_ptr = tl.user_ptr.as<int64_t>(); a.old_j = tl.csr_j.as<int32_t>(); a.old_r = tl.csr_r.as<uint8_t>();
+  a.nbr = d_nbr;
+  a.bh0 = B[7].as<float>();
+  a.U = p->U; a.V = p->V; a.b = p->b; a.bh = p->bh; a.W = p->W; a.C = p->C;
+  a.mu = float(p->mu);
+  a.inv_scale = 1.0f / c.rating_scale;
+  a.M = M; a.N = N; a.Mt = Mt; a.Nt = Nt;
+  a.F = c.F; a.K = c.K;
+  tl.ready = false;   // the training layout describes the model before the update
+  const int fpl = (c.F + 31) / 32, kpl = (c.K + 31) / 32;
+  lshmf_status s;
+  if (fpl <= 1) s = kpl <= 1 ? run_local_sgd<1, 1>(h, a, epochs, st) : run_local_sgd<1, 2>(h, a, epochs, st);
+  else if (fpl <= 2) s = kpl <= 1 ? run_local_sgd<2, 1>(h, a, epochs, st) : run_local_sgd<2, 2>(h, a, epochs, st);
+  else if (fpl <= 4) s = kpl <= 1 ? run_local_sgd<4, 1>(h, a, epochs, st) : run_local_sgd<4, 2>(h, a, epochs, st);
+  else s = kpl <= 1 ? run_local_sgd<8, 1>(h, a, epochs, st) : run_local_sgd<8, 2>(h, a, epochs, st);
+  LSHMF_TRY(s);
+  return check_device_flag(h, st, "ingest");
+}
+
+}  // namespace lshmf

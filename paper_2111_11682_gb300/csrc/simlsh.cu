@@ -167,7 +167,7 @@ template <int W, class ACC>
 __global__ void __launch_bounds__(32 * SIG_WARPS)
 k_sig_main(const int64_t *col_ptr, const int32_t *row, const uint8_t *r, const uint64_t *H,
            int hstride, int64_t N, int L, int bits, int psi_pow, const int64_t *unit_start, int64_t nunits,
-           const int64_t *split_idx, ACC *acc, uint32_t *sig) {
+           const int64_t *split_idx, ACC *acc, uint32_t *sig, int64_t *sums) {
   const int lane = threadIdx.x & 31;
   const int64_t u = int64_t(blockIdx.x) * SIG_WARPS + (threadIdx.x >> 5);
   if (u >= nunits) return;
@@ -212,7 +212,11 @@ k_sig_main(const int64_t *col_ptr, const int32_t *row, const uint8_t *r, const u
   if (nsub == 1) {
     bool bit[2 * W];
 #pragma unroll
-    for (int s = 0; s < 2 * W; ++s) bit[s] = (2 * a[s] - tot) >= 0;   // Upsilon(sum Psi * Phi)
+    for (int s = 0; s < 2 * W; ++s) {
+      const ACC sum = 2 * a[s] - tot;   // sum Psi * Phi over the item's raters
+      bit[s] = sum >= 0;                // Upsilon
+      sums[j * (64 * W) + 64 * (s >> 1) + 32 * (s & 1) + lane] = int64_t(sum);
+    }
     emit_keys<W>(bit, j, N, L, bits, sig);
   } else {
     ACC *dst = acc + split_idx[j] * (64 * W + 1);
@@ -224,7 +228,7 @@ k_sig_main(const int64_t *col_ptr, const int32_t *row, const uint8_t *r, const u
 
 template <int W, class ACC>
 __global__ void k_sig_finalize(const int64_t *unit_start, const int64_t *split_idx, int64_t N, int L,
-                               int bits, const ACC *acc, uint32_t *sig) {
+                               int bits, const ACC *acc, uint32_t *sig, int64_t *sums) {
   const int lane = threadIdx.x & 31;
   const int64_t j = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= N) return;
@@ -233,14 +237,46 @@ __global__ void k_sig_finalize(const int64_t *unit_start, const int64_t *split_i
   const ACC tot = src[64 * W];
   bool bit[2 * W];
 #pragma unroll
-  for (int s = 0; s < 2 * W; ++s) bit[s] = (2 * src[64 * (s >> 1) + 32 * (s & 1) + lane] - tot) >= 0;
+  for (int s = 0; s < 2 * W; ++s) {
+    const ACC sum = 2 * src[64 * (s >> 1) + 32 * (s & 1) + lane] - tot;
+    bit[s] = sum >= 0;
+    sums[j * (64 * W) + 64 * (s >> 1) + 32 * (s & 1) + lane] = int64_t(sum);
+  }
   emit_keys<W>(bit, j, N, L, bits, sig);
+}
+
+// Keys of items [0, N) from kept pre-sign sums (the online update, Sec. 4.3).
+template <int W>
+__global__ void k_keys_from_sums(const int64_t *sums, int64_t N, int L, int bits, uint32_t *sig) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= N) return;
+  bool bit[2 * W];
+#pragma unroll
+  for (int s = 0; s < 2 * W; ++s) bit[s] = sums[j * (64 * W) + 64 * (s >> 1) + 32 * (s & 1) + lane] >= 0;
+  emit_keys<W>(bit, j, N, L, bits, sig);
+}
+
+lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, uint32_t *sig, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  const unsigned g = (unsigned)std::max<int64_t>(1, ceil_div(N, 8));
+  switch (W) {
+    case 1: LSHMF_LAUNCH(h, k_keys_from_sums<1>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    case 2: LSHMF_LAUNCH(h, k_keys_from_sums<2>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    case 3: LSHMF_LAUNCH(h, k_keys_from_sums<3>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    case 4: LSHMF_LAUNCH(h, k_keys_from_sums<4>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    case 8: LSHMF_LAUNCH(h, k_keys_from_sums<8>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    case 16: LSHMF_LAUNCH(h, k_keys_from_sums<16>, g, 256, 0, st, sums, N, c.L, c.bits, sig); break;
+    default: return set_err(h, LSHMF_EINVAL, "internal: unsupported padded word count %d", W);
+  }
+  return LSHMF_OK;
 }
 
 template <int W, class ACC>
 static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
                                    const uint64_t *H, const int64_t *unit_start, int64_t nunits,
-                                   const int64_t *split_idx, int64_t nsplit, uint32_t *sig, cudaStream_t st) {
+                                   const int64_t *split_idx, int64_t nsplit, uint32_t *sig, int64_t *sums,
+                                   cudaStream_t st) {
   const lshmf_config &c = h->cfg;
   const int64_t accn = std::max<int64_t>(1, nsplit) * (64 * W + 1);
   LSHMF_TRY(ensure(h, h->tmp[4], accn * sizeof(ACC), "signature accumulators"));
@@ -248,24 +284,24 @@ static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int3
   LSHMF_CUDA(h, cudaMemsetAsync(acc, 0, accn * sizeof(ACC), st));
   LSHMF_LAUNCH(h, (k_sig_main<W, ACC>), (unsigned)ceil_div(nunits, SIG_WARPS), 32 * SIG_WARPS, 0, st,
                col_ptr, row, r, H, (c.L * c.bits + 63) / 64, c.N, c.L, c.bits, c.psi_pow, unit_start, nunits,
-               split_idx, acc, sig);
+               split_idx, acc, sig, sums);
   if (nsplit > 0)
     LSHMF_LAUNCH(h, (k_sig_finalize<W, ACC>), (unsigned)ceil_div(c.N, 8), 256, 0, st, unit_start, split_idx,
-                 c.N, c.L, c.bits, acc, sig);
+                 c.N, c.L, c.bits, acc, sig, sums);
   return LSHMF_OK;
 }
 
 template <class ACC>
 static lshmf_status dispatch_sig(Handle *h, int W, const int64_t *col_ptr, const int32_t *row,
                                  const uint8_t *r, const uint64_t *H, const int64_t *us, int64_t nu,
-                                 const int64_t *si, int64_t ns, uint32_t *sig, cudaStream_t st) {
+                                 const int64_t *si, int64_t ns, uint32_t *sig, int64_t *sums, cudaStream_t st) {
   switch (W) {
-    case 1: return run_signatures<1, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 2: return run_signatures<2, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 3: return run_signatures<3, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 4: return run_signatures<4, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 8: return run_signatures<8, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
-    case 16: return run_signatures<16, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, st);
+    case 1: return run_signatures<1, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 2: return run_signatures<2, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 3: return run_signatures<3, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 4: return run_signatures<4, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 8: return run_signatures<8, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 16: return run_signatures<16, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
     default: return set_err(h, LSHMF_EINVAL, "internal: unsupported padded word count %d", W);
   }
 }
@@ -595,15 +631,29 @@ lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *
   double bound = 1.0;
   for (int q = 0; q < c.psi_pow; ++q) bound *= double(hb[1]);
   bound *= 2.0 * double(std::max<int64_t>(1, hb[0]));
-  // --- signatures into tmp sig buffer (L x N)
+  // --- signatures into tmp sig buffer (L x N); the handle keeps the pre-sign sums
+  // (N x 64W, int64) for the online update (Sec. 4.3)
   LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * N + 16, "signatures"));
   uint32_t *sig = h->tmp[0].as<uint32_t>();
+  h->lsh.ready = false;
+  LSHMF_TRY(ensure(h, h->lsh.sums, sizeof(int64_t) * 64 * W * N, "kept signature sums"));
+  int64_t *sums = h->lsh.sums.as<int64_t>();
   if (bound < 2147483647.0)
-    LSHMF_TRY(dispatch_sig<int32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, st));
+    LSHMF_TRY(dispatch_sig<int32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, sums, st));
   else
-    LSHMF_TRY(dispatch_sig<int64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, st));
+    LSHMF_TRY(dispatch_sig<int64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, sums, st));
+  h->lsh.W = W;
+  h->lsh.N = N;
+  h->lsh.ready = true;
   if (sig_out)
     LSHMF_CUDA(h, cudaMemcpyAsync(sig_out, sig, sizeof(uint32_t) * c.L * N, cudaMemcpyDeviceToDevice, st));
+  return topk_from_sig(h, sig, N, nbr, st);
+}
+
+// Top-K rows (Alg. 1, lines 10-12) of all N items from their keys sig (L x N),
+// into nbr (N x K).  Uses the handle's scratch tmp[1..5] and aux.
+lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *nbr, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
 
   // --- classes of identical keys: sort items by a 64-bit hash of their L keys
   const int64_t nL = int64_t(c.L) * N;

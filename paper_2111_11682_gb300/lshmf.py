@@ -21,7 +21,7 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
-           "lshmf_rmse_noalloc"]
+           "lshmf_ingest", "lshmf_rmse_noalloc"]
 
 
 class LshmfError(RuntimeError):
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         "lshmf_predict": ([P, CP, P, P, I64, P, P], ctypes.c_int),
         "lshmf_rmse": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_rmse_noalloc": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lshmf_ingest": ([P, I64, I64, P, P, P, I64, P, P, P, CP, I32, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +248,18 @@ class LshMF:
                                       ctypes.byref(out), _stream(stream)))
         return out.value
 
+
+    def ingest(self, M_new, N_new, i, j, r, H, nbr, p: Params, local_epochs=1, want_sig=False, stream=None):
+        """lshmf_ingest (Sec. 4.3, Alg. 4).  nbr: [(N + N_new) x K] int32 (rows of new items written);
+        p: parameters sized for the enlarged model.  The handle's config grows by M_new, N_new."""
+        c = self.cfg
+        sig = torch.empty((c.L, c.N + N_new), dtype=torch.int32, device=nbr.device) if want_sig else None
+        cp = p._c()
+        self._chk(self.lib.lshmf_ingest(self.h, M_new, N_new, _ptr(i), _ptr(j), _ptr(r), i.numel(), _ptr(H),
+                                        _ptr(nbr), _ptr(sig), ctypes.byref(cp), local_epochs, _stream(stream)))
+        c.M += M_new
+        c.N += N_new
+        return sig
 
     def rmse_noalloc(self, p: Params, users, items, r, stream=None) -> float:
         """lshmf_rmse_noalloc: same result as rmse() without any device allocation."""
