@@ -5,8 +5,8 @@
 // a new item.
 //   signatures (Alg. 4 lines 1-6): the kept integer pre-sign sums of every
 //     item (Eq. 3 before Upsilon, kept by the neighbour build) receive
-//     Psi(r) (2 H_i - 1) of every new rating by integer atomics (exact, any
-//     order); keys of all items are re-derived from the sums.
+//     Psi(r) (2 H_i - 1) of every new rating, summed per item in int64 (exact,
+//     any order); keys of all items are re-derived from the sums.
 //   neighbours (lines 7-9): top-K rows of the new items over all items, from
 //     those keys; old items keep their rows.
 //   local SGD (lines 10-15), for each of `local_epochs` loops t (Eq. 7 at t):
@@ -57,23 +57,29 @@ __global__ void k_ing_ptr(const uint64_t *ks, int64_t n, uint64_t div, int64_t G
   }
 }
 
-// Alg. 4 lines 1-6: sums[j][b] += Psi(r) (2 H_i[b] - 1), one warp per rating.
-__global__ void k_ing_sums(const int32_t *ii, const int32_t *jj, const uint8_t *r, int64_t n, const uint64_t *H,
-                           int hstride, int W, int psi_pow, int64_t *sums) {
+// Alg. 4 lines 1-6: sums[j][b] += sum over the item's new ratings of
+// Psi(r) (2 H_i[b] - 1).  One warp per item (the increment in item order):
+// lane l accumulates bits l and l + 32 of each 64-bit hash word exactly in
+// int64, then adds once (no other warp touches the item).
+__global__ void k_ing_sums(const int64_t *ni_ptr, const int32_t *ni_i, const uint8_t *ni_r, int64_t Nt,
+                           const uint64_t *H, int hstride, int W, int psi_pow, int64_t *sums) {
   const int lane = threadIdx.x & 31;
-  for (int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < n;
-       p += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    const int64_t i = ii[p], j = jj[p];
-    int64_t ps = 1;
-    for (int q = 0; q < psi_pow; ++q) ps *= int64_t(r[p]);
+  for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < Nt;
+       j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int64_t p0 = ni_ptr[j], p1 = ni_ptr[j + 1];
+    if (p0 == p1) continue;
     for (int w = 0; w < W; ++w) {
-      const uint64_t hw = w < hstride ? H[i * hstride + w] : 0ull;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int64_t v = ((hw >> (32 * half + lane)) & 1ull) ? ps : -ps;
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sums[j * (64 * W) + 64 * w + 32 * half + lane]),
-                  (unsigned long long)v);
+      int64_t a0 = 0, a1 = 0;
+      for (int64_t p = p0; p < p1; ++p) {
+        const int64_t i = ni_i[p];
+        int64_t ps = 1;
+        for (int q = 0; q < psi_pow; ++q) ps *= int64_t(ni_r[p]);
+        const uint64_t hw = w < hstride ? H[i * hstride + w] : 0ull;
+        a0 += ((hw >> lane) & 1ull) ? ps : -ps;
+        a1 += ((hw >> (32 + lane)) & 1ull) ? ps : -ps;
       }
+      sums[j * (64 * W) + 64 * w + lane] += a0;
+      sums[j * (64 * W) + 64 * w + 32 + lane] += a1;
     }
   }
 }
@@ -110,6 +116,8 @@ struct IngArgs {
   const uint8_t *old_r;
   const int32_t *nbr;    // Nt x K
   const float *bh0;      // bhat at the start of the item pass
+  uint32_t *xm;          // per rating of the increment (item order): R^K mask, 2 words
+  uint8_t *xr;           // per rating: the rater's rating of each neighbour k (K bytes)
   float *U, *V, *b, *bh, *W, *C;
   float mu, inv_scale;
   float gam[6], lam[6];
@@ -186,7 +194,46 @@ __global__ void k_ing_users(const IngArgs a) {
   }
 }
 
-// Alg. 4 lines 13-15: one warp per new item; users fixed.
+// Neighbour data of the ratings of new items (users are fixed in the item
+// pass, so R^K(i; j) and the neighbour ratings can be looked up in parallel
+// before the item chains run): one warp per rating, lane <-> neighbour k.
+template <int KPL>
+__global__ void k_ing_nbr_pre(const IngArgs a) {
+  const int lane = threadIdx.x & 31, K = a.K;
+  const int64_t p0 = a.ni_ptr[a.N], p1 = a.ni_ptr[a.Nt];
+  for (int64_t p = p0 + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); p < p1;
+       p += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int64_t i = a.ni_i[p];
+    // item of rating p: the increment is in item order, so search ni_ptr
+    int64_t lo = a.N, hi = a.Nt;
+    while (hi - lo > 1) {
+      const int64_t m = (lo + hi) >> 1;
+      if (a.ni_ptr[m] <= p) lo = m;
+      else hi = m;
+    }
+    const int64_t j = lo;
+    const int64_t nlo = a.nu_ptr[i], nhi = a.nu_ptr[i + 1];
+    const int64_t olo = i < a.M ? a.old_ptr[i] : 0, ohi = i < a.M ? a.old_ptr[i + 1] : 0;
+#pragma unroll
+    for (int kk = 0; kk < KPL; ++kk) {
+      const int k = lane + 32 * kk;
+      int rq = -1;
+      if (k < K) {
+        const int32_t q = a.nbr[j * K + k];
+        rq = find_in(a.old_j, a.old_r, olo, ohi, q);
+        if (rq < 0) rq = find_in(a.nu_j, a.nu_r, nlo, nhi, q);
+        a.xr[p * K + k] = uint8_t(rq < 0 ? 0 : rq);
+      }
+      const uint32_t mk = __ballot_sync(0xffffffffu, rq >= 0);
+      if (lane == 0) a.xm[2 * p + kk] = mk;
+    }
+    if (KPL == 1 && lane == 0) a.xm[2 * p + 1] = 0u;
+  }
+}
+
+// Alg. 4 lines 13-15: one warp per new item; users fixed.  The rater's data of
+// the next rating is loaded while the current one runs (it does not depend on
+// the item chain).
 template <int FPL, int KPL>
 __global__ void k_ing_items(const IngArgs a) {
   const int lane = threadIdx.x & 31, F = a.F, K = a.K;
@@ -194,8 +241,7 @@ __global__ void k_ing_items(const IngArgs a) {
   const float l_bh = a.lam[1], l_v = a.lam[3], l_w = a.lam[4], l_c = a.lam[5];
   for (int64_t j = a.N + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); j < a.Nt;
        j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    float v[FPL], w[KPL], c[KPL];
-    int32_t q[KPL];
+    float v[FPL], w[KPL], c[KPL], bq[KPL];
 #pragma unroll
     for (int f = 0; f < FPL; ++f) v[f] = lane * FPL + f < F ? a.V[j * F + lane * FPL + f] : 0.f;
 #pragma unroll
@@ -203,39 +249,58 @@ __global__ void k_ing_items(const IngArgs a) {
       const int k = lane + 32 * kk;
       w[kk] = k < K ? a.W[j * K + k] : 0.f;
       c[kk] = k < K ? a.C[j * K + k] : 0.f;
-      q[kk] = k < K ? a.nbr[j * K + k] : 0;
+      bq[kk] = k < K ? a.bh0[a.nbr[j * K + k]] : 0.f;
     }
-    float bhj = a.bh[j];
-    for (int64_t p = a.ni_ptr[j]; p < a.ni_ptr[j + 1]; ++p) {
-      const int64_t i = a.ni_i[p];
-      const float r = float(a.ni_r[p]) * a.inv_scale;
-      const float bi = a.b[i];
-      float u[FPL];
+    int nV = 0;
 #pragma unroll
-      for (int f = 0; f < FPL; ++f) u[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
-      const int64_t nlo = a.nu_ptr[i], nhi = a.nu_ptr[i + 1];
-      const int64_t olo = i < a.M ? a.old_ptr[i] : 0, ohi = i < a.M ? a.old_ptr[i + 1] : 0;
-      float xk[KPL];
-      bool exk[KPL];
-      float sxw = 0.f, sc = 0.f, dot = 0.f;
-      int nR = 0, nV = 0;
+    for (int kk = 0; kk < KPL; ++kk) nV += __popc(__ballot_sync(0xffffffffu, lane + 32 * kk < K));
+    float bhj = a.bh[j];
+    const int64_t p0 = a.ni_ptr[j], p1 = a.ni_ptr[j + 1];
+    // operands of rating p: rater's u, b; mask; neighbour ratings; the rating
+    float un[FPL], bn = 0.f, rn = 0.f;
+    uint32_t mn[KPL];
+    uint8_t xn[KPL];
+    auto load = [&](int64_t p) {
+      const int64_t i = a.ni_i[p];
+      bn = a.b[i];
+      rn = float(a.ni_r[p]) * a.inv_scale;
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) un[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
 #pragma unroll
       for (int kk = 0; kk < KPL; ++kk) {
         const int k = lane + 32 * kk;
-        const bool valid = k < K;
-        int rq = -1;
-        if (valid) {
-          rq = find_in(a.old_j, a.old_r, olo, ohi, q[kk]);
-          if (rq < 0) rq = find_in(a.nu_j, a.nu_r, nlo, nhi, q[kk]);
-        }
-        const bool ex = rq >= 0;
-        const float x = ex ? float(rq) * a.inv_scale - (a.mu + bi + a.bh0[q[kk]]) : 0.f;
+        mn[kk] = a.xm[2 * p + kk];
+        xn[kk] = k < K ? a.xr[p * K + k] : 0;
+      }
+    };
+    if (p0 < p1) load(p0);
+    for (int64_t p = p0; p < p1; ++p) {
+      float u[FPL];
+      uint32_t mk[KPL];
+      uint8_t xb[KPL];
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) u[f] = un[f];
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        mk[kk] = mn[kk];
+        xb[kk] = xn[kk];
+      }
+      const float bi = bn, r = rn;
+      if (p + 1 < p1) load(p + 1);
+      float xk[KPL];
+      bool exk[KPL];
+      float sxw = 0.f, sc = 0.f, dot = 0.f;
+      int nR = 0;
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const bool valid = lane + 32 * kk < K;
+        const bool ex = (mk[kk] >> lane) & 1u;
+        const float x = ex ? float(xb[kk]) * a.inv_scale - (a.mu + bi + bq[kk]) : 0.f;
         xk[kk] = x;
         exk[kk] = ex;
         sxw = fmaf(x, w[kk], sxw);
         sc += (valid && !ex) ? c[kk] : 0.f;
-        nR += __popc(__ballot_sync(0xffffffffu, ex));
-        nV += __popc(__ballot_sync(0xffffffffu, valid));
+        nR += __popc(mk[kk]);
       }
 #pragma unroll
       for (int f = 0; f < FPL; ++f) dot = fmaf(u[f], v[f], dot);
@@ -275,6 +340,8 @@ static lshmf_status run_local_sgd(Handle *h, IngArgs a, int epochs, cudaStream_t
   const int64_t nu = a.Mt - a.M, ni = a.Nt - a.N;
   const unsigned gu = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nu, 8), 16L * h->num_sms));
   const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ni, 8), 16L * h->num_sms));
+  // neighbour data of the ratings of new items (fixed for the whole update: users and rows do not change)
+  if (ni > 0 && epochs > 0) LSHMF_LAUNCH(h, (k_ing_nbr_pre<KPL>), 16 * h->num_sms, 256, 0, st, a);
   for (int t = 0; t < epochs; ++t) {
     const double tfac = 1.0 + double(c.beta) * std::pow(double(t), 1.5);   // Eq. (7)
     for (int g = 0; g < 6; ++g) {
@@ -316,7 +383,8 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   LSHMF_TRY(ensure(h, B[4], sizeof(int64_t) * (Mt + 1) + 5 * nn + 128, "ingest user order"));
   LSHMF_TRY(ensure(h, B[5], sizeof(int64_t) * (Nt + 1) + 5 * nn + 128, "ingest item order"));
   LSHMF_TRY(ensure(h, B[6], sizeof(int32_t) * Nt * c.K + 64, "ingest rows"));
-  LSHMF_TRY(ensure(h, B[7], sizeof(float) * Nt + 64, "ingest bhat snapshot"));
+  LSHMF_TRY(ensure(h, B[7], sizeof(float) * Nt + sizeof(uint32_t) * 2 * nn + size_t(c.K) * nn + 128,
+                   "ingest bhat snapshot and neighbour data"));
   uint64_t *ku = B[1].as<uint64_t>(), *kus = ku + nn, *ki = B[2].as<uint64_t>(), *kis = ki + nn;
   uint32_t *vu = B[3].as<uint32_t>(), *vus = vu + nn, *vi = vus + nn, *vis = vi + nn;
   int64_t *nu_ptr = B[4].as<int64_t>();
@@ -344,9 +412,9 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   LSHMF_CUDA(h, cudaMemcpyAsync(sums, S.sums.p, sizeof(int64_t) * 64 * W * N, cudaMemcpyDeviceToDevice, st));
   LSHMF_CUDA(h, cudaMemsetAsync(sums + 64 * W * N, 0, sizeof(int64_t) * 64 * W * (Nt - N), st));
   if (n > 0) {
-    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), 16L * h->num_sms));
-    LSHMF_LAUNCH(h, k_ing_sums, gs, 256, 0, st, d_i, d_j, d_r, n, d_H, (c.L * c.bits + 63) / 64, W, c.psi_pow,
-                 sums);
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(Nt, 8), 16L * h->num_sms));
+    LSHMF_LAUNCH(h, k_ing_sums, gs, 256, 0, st, ni_ptr, ni_i, ni_r, Nt, d_H, (c.L * c.bits + 63) / 64, W,
+                 c.psi_pow, sums);
   }
   // the handle now describes the enlarged model
   c.M = Mt;
@@ -372,6 +440,8 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   a.old_ptr = tl.user_ptr.as<int64_t>(); a.old_j = tl.csr_j.as<int32_t>(); a.old_r = tl.csr_r.as<uint8_t>();
   a.nbr = d_nbr;
   a.bh0 = B[7].as<float>();
+  a.xm = reinterpret_cast<uint32_t *>(B[7].as<char>() + ((sizeof(float) * Nt + 15) & ~size_t(15)));
+  a.xr = reinterpret_cast<uint8_t *>(a.xm + 2 * nn);
   a.U = p->U; a.V = p->V; a.b = p->b; a.bh = p->bh; a.W = p->W; a.C = p->C;
   a.mu = float(p->mu);
   a.inv_scale = 1.0f / c.rating_scale;
