@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--P", type=int, default=0, help="strata (0 = workload default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-ingest", action="store_true", help="skip the online-update measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the top-N and online-update measurements")
     return ap.parse_args()
 
 
@@ -135,6 +135,31 @@ def sgd_bytes_per_epoch(stats, w):
     plus one byte per explicit neighbour rating."""
     nnz = stats["nnz"]
     return nnz * (4 + 1 + w.K / 8 + 8 * w.F + 8) + stats["explicit_neighbours"]
+
+
+def measure_topn(m, p, w, dev, sizes=(1, 64, 1024, 4096), reps=20, n=10, seed=0):
+    """Top-N serving (lshmf_topn, Eq. (1) over all items, FP32): latency of one call for batches
+    of query users of several sizes (users drawn uniformly, inputs resident in HBM)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    out = {"what": "lshmf_topn (Eq. 1 over all unrated items, FP32, top-%d)" % n, "batches": []}
+    for bs in sizes:
+        users = torch.from_numpy(rng.integers(0, w.M, (reps + 2, bs)).astype(np.int32)).to(dev)
+        ms = []
+        for r in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            m.topn(p, users[r], n)
+            b.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ms.append(a.elapsed_time(b))
+        ms = np.array(ms)
+        out["batches"].append({"users": bs, "p50_ms": round(float(np.percentile(ms, 50)), 4),
+                               "p99_ms": round(float(np.percentile(ms, 99)), 4),
+                               "items_scored_per_s": bs * w.N / (float(np.median(ms)) / 1e3)})
+    return out
 
 
 def measure_ingest(w, d, P, dev, reps=3, frac=0.01, local_epochs=1):
@@ -287,8 +312,11 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * E * nnz / (ms_e2e / 1e3), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
 
+    topn = None
+    if rank == 0 and not args.no_serving:
+        topn = measure_topn(m, p, w, dev)
     ingest = None
-    if rank == 0 and not args.no_ingest:
+    if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
 
@@ -315,7 +343,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
            "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
-           "ingest": ingest,
+           "topn": topn, "ingest": ingest,
            "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)

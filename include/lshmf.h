@@ -15,6 +15,7 @@
  *                           with the learning rate of Eq. (7) (Alg. 3)
  *   lshmf_predict/_rmse     Eq. (1) on query pairs, Eq. (6)
  *   lshmf_ingest            the online update of Sec. 4.3 (Alg. 4)
+ *   lshmf_topn              top-N recommendation by Eq. (1)
  *
  * Conventions shared by every entry point:
  *  - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
@@ -190,6 +191,18 @@ lshmf_status lshmf_ingest(lshmf_handle *h, int64_t M_new, int64_t N_new, const i
                           const int32_t *d_j, const uint8_t *d_r, int64_t n, const uint64_t *d_H,
                           int32_t *d_nbr, uint32_t *d_sig, const lshmf_params *p, int32_t local_epochs,
                           void *stream);
+
+/* Top-N recommendation by Eq. (1).  For each query user d_users[q] (int32, n
+ * of them): the prediction of Eq. (1) (Sec. 3.2) for every item the user did
+ * not rate in the prepared training set, with neighbour baselines from the
+ * current bhat (nothing is updated), and the topn items with the highest
+ * scores, ordered by (score desc, item asc).  d_items_out int32 [n x topn],
+ * d_scores_out float32 [n x topn]; slots past the number of unrated items hold
+ * item -1 and score -infinity.  mode 0: FP32 (the only mode).  topn in [1, 1024];
+ * N <= 32768 (scores and the user's ratings are held in shared memory; EINVAL
+ * above).  Requires lshmf_prepare_training.  Asynchronous. */
+lshmf_status lshmf_topn(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n,
+                        int32_t topn, int32_t mode, int32_t *d_items_out, float *d_scores_out, void *stream);
 
 /* Sizes of the prepared training layout (for memory planning and for the
  * algorithmic byte count of an epoch: every rating reads its user slot,

@@ -59,6 +59,7 @@ def _load():
         "oracle_rating_step": [I32, I32, D, D, P, P, P, P, P, P, P, P, P, P, P],
         "oracle_train": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I32, I32, I32, P],
         "oracle_ingest_sgd": [CP, I64, I64, I64, P, P, P, I64, P, P, P, P, D, P, P, P, P, P, P, I32],
+        "oracle_topn": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, I32, P, P],
         "oracle_predict": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P],
         "oracle_rmse": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P, P],
         "oracle_loss": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, P],
@@ -241,6 +242,17 @@ def predict(cfg, ti, tj, tr, nbr, mu, params: Params, qi, qj):
     _check(_load().oracle_predict(ctypes.byref(cfg), len(ti), _p(ti), _p(tj), _p(tr), _p(nbr), mu,
                                   *params.ptrs(), len(qi), _p(qi), _p(qj), _p(out)), "predict")
     return out
+
+
+def topn(cfg, ti, tj, tr, nbr, mu, params: Params, users, n):
+    """Eq. (1) top-n unrated items per query user: (items [q x n] int32, scores [q x n] float64)."""
+    ti, tj, tr, nbr = _c(ti, np.int32), _c(tj, np.int32), _c(tr, np.uint8), _c(nbr, np.int32)
+    users = _c(users, np.int32)
+    items = np.zeros((len(users), n), np.int32)
+    scores = np.zeros((len(users), n), np.float64)
+    _check(_load().oracle_topn(ctypes.byref(cfg), len(ti), _p(ti), _p(tj), _p(tr), _p(nbr), mu, *params.ptrs(),
+                               len(users), _p(users), n, _p(items), _p(scores)), "topn")
+    return items, scores
 
 
 def rmse(cfg, ti, tj, tr, nbr, mu, params: Params, qi, qj, qr):

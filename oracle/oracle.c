@@ -14,6 +14,7 @@
  *   oracle_train                                Sec. 4.2, Alg. 3 with the
  *                                               stratified P x P block schedule
  *   oracle_predict / oracle_rmse / oracle_loss  Eq. (1), Eq. (6), Eq. (2)
+ *   oracle_topn                                 Eq. (1) top-N recommendation
  *   oracle_ingest_sgd                           Sec. 4.3, Alg. 4 local SGD of the
  *                                               online update
  *
@@ -584,6 +585,49 @@ int oracle_predict(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const in
     int32_t nR, nN;
     out[p] = predict_one(c->F, c->K, mu, U + i * c->F, V + j * c->F, b[i], bh[j], W + j * c->K,
                          C + j * c->K, nbi, x, &nR, &nN);
+  }
+  free_user_lists(&ul);
+  return ORC_OK;
+}
+
+/* Top-N recommendation by Eq. (1): for each query user qu[q], the topn items
+ * with the highest predicted rating among the items the user did not rate in
+ * the training set, ordered by (score desc, item asc); neighbour baselines use
+ * the current bhat (nothing is updated).  items/scores are nq x topn; slots
+ * past the number of unrated items hold item -1 and score -infinity. */
+int oracle_topn(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int32_t *tj, const uint8_t *tr,
+                const int32_t *nbr, double mu, const double *U, const double *V, const double *b, const double *bh,
+                const double *W, const double *C, int64_t nq, const int32_t *qu, int32_t topn, int32_t *items,
+                double *scores) {
+  const int64_t M = c->M, N = c->N;
+  const int32_t F = c->F, K = c->K;
+  if (F <= 0 || K <= 0 || F > 1024 || K > 1024 || topn <= 0) return ORC_EINVAL;
+  if (validate(M, N, nnz, ti, tj) != ORC_OK) return ORC_EINVAL;
+  for (int64_t q = 0; q < nq; ++q)
+    if (qu[q] < 0 || qu[q] >= M) return ORC_EINVAL;
+  user_lists ul;
+  if (build_user_lists(M, nnz, ti, tj, tr, &ul) != ORC_OK) return ORC_ENOMEM;
+  uint8_t expl[1024];
+  double rnb[1024], bnb[1024], x[1024];
+  for (int64_t q = 0; q < nq; ++q) {
+    const int64_t i = qu[q];
+    int32_t *it = items + q * topn;
+    double *sc = scores + q * topn;
+    for (int32_t t = 0; t < topn; ++t) { it[t] = -1; sc[t] = -INFINITY; }
+    for (int64_t j = 0; j < N; ++j) {
+      if (user_rating(&ul, i, (int32_t)j) >= 0) continue;   /* rated in training: not recommended */
+      neighbours_of(c, &ul, i, j, nbr, bh, expl, rnb, bnb);
+      nb_info nb = {expl, rnb, bnb};
+      int32_t nR, nN;
+      double s = predict_one(F, K, mu, U + i * F, V + j * F, b[i], bh[j], W + j * K, C + j * K, nb, x, &nR, &nN);
+      /* insert keeping (score desc, item asc); items arrive in ascending order */
+      int32_t pos = topn;
+      while (pos > 0 && (it[pos - 1] < 0 || sc[pos - 1] < s)) --pos;
+      if (pos >= topn) continue;
+      for (int32_t t = topn - 1; t > pos; --t) { it[t] = it[t - 1]; sc[t] = sc[t - 1]; }
+      it[pos] = (int32_t)j;
+      sc[pos] = s;
+    }
   }
   free_user_lists(&ul);
   return ORC_OK;

@@ -13,6 +13,8 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
                           cudaStream_t st);
 lshmf_status predict(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, int64_t n, float *out,
                      cudaStream_t st);
+lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_, int32_t mode,
+                  int32_t *d_items, float *d_scores, cudaStream_t st);
 lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i, const int32_t *d_j,
                     const uint8_t *d_r, int64_t n, const uint64_t *d_H, int32_t *d_nbr, uint32_t *d_sig,
                     const lshmf_params *p, int32_t epochs, cudaStream_t st);
@@ -160,6 +162,12 @@ lshmf_status lshmf_ingest(lshmf_handle *hh, int64_t M_new, int64_t N_new, const 
   if (M_new < 0 || N_new < 0) return set_err(h, LSHMF_EINVAL, "ingest: negative new user/item count");
   if (h->cfg.K >= h->cfg.N + N_new) return set_err(h, LSHMF_EINVAL, "ingest: K must be < N");
   return ingest(h, M_new, N_new, d_i, d_j, d_r, n, d_H, d_nbr, d_sig, p, local_epochs, S(stream));
+}
+
+lshmf_status lshmf_topn(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_,
+                        int32_t mode, int32_t *d_items_out, float *d_scores_out, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  return topn(&hh->h, p, d_users, n, topn_, mode, d_items_out, d_scores_out, S(stream));
 }
 
 lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out) {

@@ -21,7 +21,7 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
-           "lshmf_ingest", "lshmf_rmse_noalloc"]
+           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc"]
 
 
 class LshmfError(RuntimeError):
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "lshmf_rmse": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_rmse_noalloc": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_ingest": ([P, I64, I64, P, P, P, I64, P, P, P, CP, I32, P], ctypes.c_int),
+        "lshmf_topn": ([P, CP, P, I64, I32, I32, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +261,16 @@ class LshMF:
         c.M += M_new
         c.N += N_new
         return sig
+
+    def topn(self, p: Params, users, n: int, mode: int = 0, stream=None):
+        """lshmf_topn: (items [q x n] int32, scores [q x n] float32) on the device."""
+        q = users.numel()
+        items = torch.empty((q, n), dtype=torch.int32, device=users.device)
+        scores = torch.empty((q, n), dtype=torch.float32, device=users.device)
+        cp = p._c()
+        self._chk(self.lib.lshmf_topn(self.h, ctypes.byref(cp), _ptr(users), q, n, mode, _ptr(items), _ptr(scores),
+                                      _stream(stream)))
+        return items, scores
 
     def rmse_noalloc(self, p: Params, users, items, r, stream=None) -> float:
         """lshmf_rmse_noalloc: same result as rmse() without any device allocation."""
