@@ -138,27 +138,39 @@ def sgd_bytes_per_epoch(stats, w):
 
 
 def measure_topn(m, p, w, dev, sizes=(1, 64, 1024, 4096), reps=20, n=10, seed=0):
-    """Top-N serving (lshmf_topn, Eq. (1) over all items, FP32): latency of one call for batches
-    of query users of several sizes (users drawn uniformly, inputs resident in HBM)."""
+    """Top-N serving (lshmf_topn, Eq. (1) over all items): latency of one call for batches of
+    query users of several sizes (users drawn uniformly, inputs resident in HBM), for the FP32
+    path (mode 0) and the BF16 tensor-core candidates + FP32 rerank path (mode 1), and the
+    recall@n of mode 1 against mode 0 on the largest batch."""
     import torch
 
     rng = np.random.default_rng(seed)
-    out = {"what": "lshmf_topn (Eq. 1 over all unrated items, FP32, top-%d)" % n, "batches": []}
-    for bs in sizes:
-        users = torch.from_numpy(rng.integers(0, w.M, (reps + 2, bs)).astype(np.int32)).to(dev)
-        ms = []
-        for r in range(reps + 2):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            m.topn(p, users[r], n)
-            b.record()
-            torch.cuda.synchronize()
-            if r >= 2:
-                ms.append(a.elapsed_time(b))
-        ms = np.array(ms)
-        out["batches"].append({"users": bs, "p50_ms": round(float(np.percentile(ms, 50)), 4),
-                               "p99_ms": round(float(np.percentile(ms, 99)), 4),
-                               "items_scored_per_s": bs * w.N / (float(np.median(ms)) / 1e3)})
+    out = {"what": "lshmf_topn: Eq. (1) over all unrated items, top-%d" % n, "modes": {}}
+    for mode, name in ((0, "fp32"), (1, "bf16_tc_candidates+fp32_rerank")):
+        rows = []
+        for bs in sizes:
+            users = torch.from_numpy(rng.integers(0, w.M, (reps + 2, bs)).astype(np.int32)).to(dev)
+            ms = []
+            for r in range(reps + 2):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                m.topn(p, users[r], n, mode=mode)
+                b.record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    ms.append(a.elapsed_time(b))
+            ms = np.array(ms)
+            rows.append({"users": bs, "p50_ms": round(float(np.percentile(ms, 50)), 4),
+                         "p99_ms": round(float(np.percentile(ms, 99)), 4),
+                         "items_scored_per_s": bs * w.N / (float(np.median(ms)) / 1e3)})
+        out["modes"][name] = rows
+    m.check()
+    users = torch.from_numpy(rng.integers(0, w.M, sizes[-1]).astype(np.int32)).to(dev)
+    i0, _ = m.topn(p, users, n, mode=0)
+    i1, _ = m.topn(p, users, n, mode=1)
+    i0, i1 = i0.cpu().numpy(), i1.cpu().numpy()
+    hits = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(i0, i1))
+    out["recall_at_%d_mode1_vs_mode0" % n] = hits / float(n * len(i0))
     return out
 
 

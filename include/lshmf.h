@@ -198,9 +198,16 @@ lshmf_status lshmf_ingest(lshmf_handle *h, int64_t M_new, int64_t N_new, const i
  * current bhat (nothing is updated), and the topn items with the highest
  * scores, ordered by (score desc, item asc).  d_items_out int32 [n x topn],
  * d_scores_out float32 [n x topn]; slots past the number of unrated items hold
- * item -1 and score -infinity.  mode 0: FP32 (the only mode).  topn in [1, 1024];
- * N <= 32768 (scores and the user's ratings are held in shared memory; EINVAL
- * above).  Requires lshmf_prepare_training.  Asynchronous. */
+ * item -1 and score -infinity.  topn in [1, 1024]; N <= 32768 (EINVAL above).
+ * mode 0: FP32 for every item (scores and the user's ratings in shared memory).
+ * mode 1: candidates from the dense part u_i.v_j + bhat_j computed with BF16
+ *   inputs and FP32 accumulation on the tensor cores, the 32 best unrated items
+ *   of each item slice per user (at most 8 slices), then the mode-0 FP32 score of
+ *   Eq. (1) for the candidates only and the topn best of them: the same scores
+ *   as mode 0 for the items it returns, and mode 0's list whenever the
+ *   candidates hold it (recall is measured, not guaranteed).  Needs topn <= 32,
+ *   F <= 256.
+ * Requires lshmf_prepare_training.  Asynchronous. */
 lshmf_status lshmf_topn(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n,
                         int32_t topn, int32_t mode, int32_t *d_items_out, float *d_scores_out, void *stream);
 

@@ -77,3 +77,27 @@ def test_topn_fill_and_errors(trained):
     with pytest.raises(LshmfError) as e:
         m.topn(p, T(np.array([0], np.int32), torch.int32), 5, mode=7)
     assert e.value.status == lshmf.EINVAL
+
+
+def test_topn_bf16_candidates_rerank(trained):
+    """Mode 1 (BF16 tensor-core candidates + FP32 rerank) returns mode-0 scores for its items and
+    reaches the mode-0 list for nearly every user."""
+    w, d, m, p, nbr = trained
+    users = np.arange(0, w.M, 7, dtype=np.int32)
+    n = 10
+    i0, s0 = m.topn(p, T(users, torch.int32), n, mode=0)
+    i1, s1 = m.topn(p, T(users, torch.int32), n, mode=1)
+    m.check()
+    i0, s0, i1, s1 = i0.cpu().numpy(), s0.cpu().numpy(), i1.cpu().numpy(), s1.cpu().numpy()
+    rated = set(zip(d["train_i"].tolist(), d["train_j"].tolist()))
+    hits = 0
+    for q, u in enumerate(users):
+        assert len(set(i1[q].tolist())) == n and all((int(u), int(j)) not in rated for j in i1[q])
+        assert np.all(np.diff(s1[q]) <= 0)
+        common = {int(j): k for k, j in enumerate(i0[q])}
+        for k, j in enumerate(i1[q]):
+            if int(j) in common:
+                assert s1[q, k] == s0[q, common[int(j)]]   # the same FP32 score function
+        hits += len(set(i0[q].tolist()) & set(i1[q].tolist()))
+    recall = hits / (n * len(users))
+    assert recall >= 0.99, recall
