@@ -166,16 +166,16 @@ lshmf_status lshmf_train_strata(lshmf_handle *h, const lshmf_params *p, int32_t 
  * items [N, N + N_new) and n ratings (d_i, d_j, d_r: int32, int32, uint8 on
  * the device), each of which has a new user or a new item (an old user with
  * an old item, an index out of range or a repeated pair: EINVAL).
- *  - Alg. 4 lines 1-6: the integer pre-sign sums of Eq. (3) that
+ *  - hash values (Alg. 4): the integer pre-sign sums of Eq. (3) that
  *    lshmf_build_neighbours kept for every item receive Psi(r) (2 H_i - 1) of
  *    each new rating; keys of all items follow from the sums (Upsilon), so they
  *    equal a neighbour build over all ratings, bit for bit.  d_H: the hash
  *    bits of all M + M_new users (the first M rows as given to the build).
- *  - lines 7-9: the top-K rows (Alg. 1 rule) of the new items over all
+ *  - neighbour search (Alg. 4): the top-K rows (Alg. 1 rule) of the new items over all
  *    N + N_new items are written to d_nbr[N .. N + N_new) (d_nbr: int32
  *    [(N + N_new) x K]; rows of old items are kept as the caller holds them).
  *    d_sig (NULL allowed): receives the keys of all items, uint32 [L x (N + N_new)].
- *  - lines 10-15, local_epochs times (learning rate of Eq. 7 at the loop index
+ *  - local SGD (Alg. 4), local_epochs times (learning rate of Eq. 7 at the loop index
  *    from 0): each new user's new ratings of old items in item order (Eq. 1, then
  *    the b and u updates of Eq. 5; items fixed), then each new item's ratings in
  *    user order (Eq. 1 with neighbour baselines from bhat at the start of the

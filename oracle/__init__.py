@@ -227,7 +227,7 @@ def train(cfg, ti, tj, tr, nbr, mu, params: Params, epoch, s_begin=0, s_end=None
 
 
 def ingest_sgd(cfg, M_old, N_old, oi, oj, orr, ni, nj, nr, nbr, mu, params: Params, epochs):
-    """Local SGD of the online update (Sec. 4.3, Alg. 4 lines 10-15), in place.
+    """Local SGD of the online update (Sec. 4.3, Alg. 4: user update, then item update), in place.
     cfg holds the sizes after the update; users >= M_old and items >= N_old are new."""
     oi, oj, orr = _c(oi, np.int32), _c(oj, np.int32), _c(orr, np.uint8)
     ni, nj, nr, nbr = _c(ni, np.int32), _c(nj, np.int32), _c(nr, np.uint8), _c(nbr, np.int32)

@@ -470,17 +470,17 @@ int oracle_train(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int3
   return ORC_OK;
 }
 
-/* Sec. 4.3, Alg. 4 (lines 10-15): the local SGD of the online update.
+/* Sec. 4.3, Alg. 4: the local SGD of the online update.
  * Users [M_old, c->M) and items [N_old, c->N) are new; c->M, c->N are the
  * sizes after the update.  The old ratings are the training set of the model
  * before the update, the new ratings those of the increment (each has a new
  * user or a new item).  nbr holds the rows of all items (the kept rows of old
  * items, the searched rows of new items).  R(i) is the user's items over old
  * and new ratings.  For loop t = 0..epochs-1 (learning rate of Eq. (7) at t):
- *   lines 10-12: new users in ascending order, each over its new ratings of
+ *   user update: new users in ascending order, each over its new ratings of
  *     OLD items in item order: Eq. (1), then the b and u updates of Eq. (5);
  *     item parameters stay as they are;
- *   lines 13-15: new items in ascending order, each over its ratings (every
+ *   item update: new items in ascending order, each over its ratings (every
  *     rating of a new item is new) in user order: Eq. (1) with neighbour
  *     baselines from the bhat of the pass start, then the bhat, v, w, c
  *     updates of Eq. (5); user parameters stay as they are.
@@ -536,7 +536,7 @@ int oracle_ingest_sgd(const oracle_cfg *c, int64_t M_old, int64_t N_old, int64_t
     double gam[6], lam[6];
     double tfac = 1.0 + c->beta * pow((double)t, 1.5);   /* Eq. (7) */
     for (int g = 0; g < 6; ++g) { gam[g] = c->alpha[g] / tfac; lam[g] = c->lambda[g]; }
-    /* lines 10-12: new users over old items; items stay fixed */
+    /* user update: new users over old items; items stay fixed */
     for (int64_t p = 0; p < n_new; ++p) {
       int64_t i = byu[p].j, j = byu[p].i;
       if (i < M_old || j >= N_old) continue;
@@ -548,7 +548,7 @@ int oracle_ingest_sgd(const oracle_cfg *c, int64_t M_old, int64_t N_old, int64_t
       oracle_rating_step(F, K, (double)byu[p].r / c->rating_scale, mu, U + i * F, sv, b + i, &sbh, sw, sc, expl,
                          rnb, bnb, gam, lam);
     }
-    /* lines 13-15: new items over all their raters; users stay fixed */
+    /* item update: new items over all their raters; users stay fixed */
     memcpy(bh0, bh, sizeof(double) * (size_t)N);
     for (int64_t p = 0; p < n_new; ++p) {
       int64_t j = byi[p].j, i = byi[p].i;

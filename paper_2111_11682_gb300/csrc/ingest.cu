@@ -3,13 +3,13 @@
 // The model was built for M users x N items; an increment brings users
 // [M, M + M_new), items [N, N + N_new) and n ratings, each with a new user or
 // a new item.
-//   signatures (Alg. 4 lines 1-6): the kept integer pre-sign sums of every
+//   hash values (Alg. 4, old and new items): the kept integer pre-sign sums of every
 //     item (Eq. 3 before Upsilon, kept by the neighbour build) receive
 //     Psi(r) (2 H_i - 1) of every new rating, summed per item in int64 (exact,
 //     any order); keys of all items are re-derived from the sums.
-//   neighbours (lines 7-9): top-K rows of the new items over all items, from
+//   neighbour search (Alg. 4, new items): top-K rows of the new items over all items, from
 //     those keys; old items keep their rows.
-//   local SGD (lines 10-15), for each of `local_epochs` loops t (Eq. 7 at t):
+//   local SGD (Alg. 4, new users then new items), for each of `local_epochs` loops t (Eq. 7 at t):
 //     one warp per new user runs the user's new ratings of old items in item
 //     order, Eq. (1) then the b and u updates of Eq. (5), items fixed; then one
 //     warp per new item runs its raters in user order, Eq. (1) with neighbour
@@ -57,7 +57,7 @@ __global__ void k_ing_ptr(const uint64_t *ks, int64_t n, uint64_t div, int64_t G
   }
 }
 
-// Alg. 4 lines 1-6: sums[j][b] += sum over the item's new ratings of
+// Hash values of Alg. 4: sums[j][b] += sum over the item's new ratings of
 // Psi(r) (2 H_i[b] - 1).  One warp per item (the increment in item order):
 // lane l accumulates bits l and l + 32 of each 64-bit hash word exactly in
 // int64, then adds once (no other warp touches the item).
@@ -135,7 +135,7 @@ __device__ __forceinline__ void warp_sum3(float &x, float &y, float &z) {
   }
 }
 
-// Alg. 4 lines 10-12: one warp per new user; items fixed.
+// User update of Alg. 4: one warp per new user; items fixed.
 template <int FPL, int KPL>
 __global__ void k_ing_users(const IngArgs a) {
   const int lane = threadIdx.x & 31, F = a.F, K = a.K;
@@ -231,7 +231,7 @@ __global__ void k_ing_nbr_pre(const IngArgs a) {
   }
 }
 
-// Alg. 4 lines 13-15: one warp per new item; users fixed.  The rater's data of
+// Item update of Alg. 4: one warp per new item; users fixed.  The rater's data of
 // the next rating is loaded while the current one runs (it does not depend on
 // the item chain).
 template <int FPL, int KPL>
@@ -407,7 +407,7 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kus, n, uint64_t(Nt), Mt, nu_ptr);
   LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kis, n, uint64_t(Mt), Nt, ni_ptr);
   LSHMF_TRY(check_device_flag(h, st, "ingest (increment: index out of range, an old user-item pair, or a duplicate)"));
-  // Alg. 4 lines 1-6: sums of the enlarged item set, then keys of all items
+  // hash values (Alg. 4): sums of the enlarged item set, then keys of all items
   int64_t *sums = B[0].as<int64_t>();
   LSHMF_CUDA(h, cudaMemcpyAsync(sums, S.sums.p, sizeof(int64_t) * 64 * W * N, cudaMemcpyDeviceToDevice, st));
   LSHMF_CUDA(h, cudaMemsetAsync(sums + 64 * W * N, 0, sizeof(int64_t) * 64 * W * (Nt - N), st));
@@ -426,14 +426,14 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   uint32_t *sig = h->tmp[0].as<uint32_t>();
   LSHMF_TRY(keys_from_sums(h, sums, W, Nt, sig, st));
   if (d_sig) LSHMF_CUDA(h, cudaMemcpyAsync(d_sig, sig, sizeof(uint32_t) * c.L * Nt, cudaMemcpyDeviceToDevice, st));
-  // lines 7-9: rows of the new items over all items; old rows are kept
+  // neighbour search (Alg. 4): rows of the new items over all items; old rows are kept
   int32_t *rows = B[6].as<int32_t>();
   LSHMF_TRY(topk_from_sig(h, sig, Nt, rows, st));
   if (N_new > 0)
     LSHMF_LAUNCH(h, k_ing_copy_rows, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N_new * c.K, 256),
                                                                                      16L * h->num_sms)),
                  256, 0, st, rows, N, N_new, c.K, d_nbr);
-  // lines 10-15: local SGD
+  // local SGD (Alg. 4)
   IngArgs a;
   a.nu_ptr = nu_ptr; a.nu_j = nu_j; a.nu_r = nu_r;
   a.ni_ptr = ni_ptr; a.ni_i = ni_i; a.ni_r = ni_r;

@@ -650,7 +650,7 @@ lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *
   return topk_from_sig(h, sig, N, nbr, st);
 }
 
-// Top-K rows (Alg. 1, lines 10-12) of all N items from their keys sig (L x N),
+// Top-K rows (the neighbour search of Alg. 1) of all N items from their keys sig (L x N),
 // into nbr (N x K).  Uses the handle's scratch tmp[1..5] and aux.
 lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *nbr, cudaStream_t st) {
   const lshmf_config &c = h->cfg;

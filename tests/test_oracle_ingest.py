@@ -4,7 +4,7 @@ Signatures of the online update are pinned by their definition: the keys of
 the enlarged rating set are those of Eq. (3) over all raters (the CUDA path's
 incremental sums are compared with them in the GPU tests); the rows of new
 items are the top-K rows of that definition.  Here the local SGD of Alg. 4
-(lines 10-15) is pinned against the hand-derived single step of Eq. (1) and
+(user update, then item update) is pinned against the hand-derived single step of Eq. (1) and
 Eq. (5) (tests/golden/sgd_single_step.txt), and against properties that its
 reading fixes: fixed sides stay fixed, new users are independent of each other
 in the user pass, the input order does not matter, zero rates change nothing.
