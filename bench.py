@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the top-N and online-update measurements")
+    ap.add_argument("--epochs", type=int, default=0, help="epochs per job (0 = the workload's; other values are for profiling only)")
     return ap.parse_args()
 
 
@@ -237,7 +238,7 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.time()
     d = synth.generate(w)
     gen_s = time.time() - t0
-    E = w.epochs
+    E = args.epochs or w.epochs
     nnz = len(d["train_i"])
     host = {k: torch.from_numpy(np.ascontiguousarray(d[k])).pin_memory()
             for k in ("train_i", "train_j", "train_r", "test_i", "test_j", "test_r", "U0", "V0")}
