@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_tc_candidates(const TcArgs a) {
   unsigned char *Bt = tsm + TC_M * a.Fp * 2;                  // TC_N x Fp BF16
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ float stash[TC_M][17];   // scores of the columns that beat the thread's threshold
   const int tid = threadIdx.x, wid = tid >> 5;
   const int64_t q0 = int64_t(blockIdx.x) * TC_M;
   const int slice = blockIdx.y;
@@ -326,34 +327,46 @@ __global__ void __launch_bounds__(TC_M, 1) k_tc_candidates(const TcArgs a) {
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      // cheap pass: which of the 16 columns beat the current threshold
+      uint32_t hit = 0;
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int64_t j = j0 + 16 * c + e;
-        if (!my_valid || j >= a.N) continue;
-        const float sc = __uint_as_float(r[e]) + a.bh[j];
+        if (my_valid && j < a.N) {
+          const float sc = __uint_as_float(r[e]) + a.bh[j];
+          if (sc > cmin) {
+            hit |= 1u << e;
+            stash[tid][e] = sc;
+          }
+        }
+      }
+      // rare pass: one copy of the insertion code for the columns that did
+      while (hit) {
+        const int e = __ffs(hit) - 1;
+        hit &= hit - 1;
+        const int64_t j = j0 + 16 * c + e;
+        const float sc = stash[tid][e];
         if (sc <= cmin) continue;
         while (cur < cend && a.csr_j[cur] < j) ++cur;
         if (cur < cend && a.csr_j[cur] == j) continue;   // rated in training
-        {
-          // replace the current minimum, then find the new one
-          int mp = 0;
-          float mv = cs[0];
+        // replace the current minimum, then find the new one
+        int mp = 0;
+        float mv = cs[0];
 #pragma unroll
-          for (int x = 1; x < TC_C; ++x)
-            if (cs[x] < mv) {
-              mv = cs[x];
-              mp = x;
-            }
+        for (int x = 1; x < TC_C; ++x)
+          if (cs[x] < mv) {
+            mv = cs[x];
+            mp = x;
+          }
 #pragma unroll
-          for (int x = 0; x < TC_C; ++x)
-            if (x == mp) {
-              cs[x] = sc;
-              cj[x] = int32_t(j);
-            }
-          cmin = cs[0];
+        for (int x = 0; x < TC_C; ++x)
+          if (x == mp) {
+            cs[x] = sc;
+            cj[x] = int32_t(j);
+          }
+        cmin = cs[0];
 #pragma unroll
-          for (int x = 1; x < TC_C; ++x) cmin = fminf(cmin, cs[x]);
-        }
+        for (int x = 1; x < TC_C; ++x) cmin = fminf(cmin, cs[x]);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
