@@ -222,6 +222,90 @@ def measure_ingest(w, d, P, dev, reps=3, frac=0.01, local_epochs=1):
             "ratings_per_s": n / (ms / 1e3)}
 
 
+def measure_serving(w, d, P, dev, frac=0.01, n_inc=4, rate=4000.0, horizon=2.0, seed=1):
+    """Serving loop (serve.Server) under a Poisson mix: top-N queries of 1-16 users (mode 1,
+    top-10) arrive at `rate` per second for `horizon` seconds, and the last `frac` of users and
+    items arrive as `n_inc` online updates spread over the horizon.  The loop merges waiting
+    queries into one call (continuous batching) and applies updates in arrival order.
+    Latency is host wall clock from submission to answer."""
+    import dataclasses
+    import threading
+
+    import torch
+
+    from paper_2111_11682_gb300 import LshMF, Params, config_from_workload
+    from paper_2111_11682_gb300.serve import Server, latency_summary, poisson_times
+
+    M_new, N_new = max(n_inc, int(w.M * frac)), max(n_inc, int(w.N * frac))
+    M_old, N_old = w.M - M_new, w.N - N_new
+    Mb = [M_old + (k + 1) * M_new // n_inc for k in range(n_inc)]
+    Nb = [N_old + (k + 1) * N_new // n_inc for k in range(n_inc)]
+    i, j, r = d["train_i"], d["train_j"], d["train_r"]
+    ku = np.searchsorted(np.array([M_old] + Mb), i, side="right") - 1   # -1: old user
+    kj = np.searchsorted(np.array([N_old] + Nb), j, side="right") - 1
+    kr = np.maximum(ku, kj)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    old = kr < 0
+    oi, oj, orr = t(i[old], torch.int32), t(j[old], torch.int32), t(r[old], torch.uint8)
+    H = t(d["H"].view(np.int64), torch.int64)
+    m = LshMF(config_from_workload(dataclasses.replace(w, M=M_old, N=N_old), P))
+    col_ptr, row, rc = m.csc_from_coo(oi, oj, orr)
+    nbr = torch.zeros((w.N, w.K), dtype=torch.int32, device=dev)
+    m.build_neighbours(col_ptr, row, rc, H[:M_old].contiguous(), nbr_out=nbr[:N_old])
+    mu = m.prepare_training(oi, oj, orr, nbr[:N_old].contiguous())
+    p = Params.from_init(d["U0"], d["V0"], w.K, dev)
+    p.mu = mu
+    del col_ptr, row, rc
+    incs = []
+    prevM, prevN = M_old, N_old
+    for k in range(n_inc):
+        sel = kr == k
+        incs.append((Mb[k] - prevM, Nb[k] - prevN, i[sel], j[sel], r[sel]))
+        prevM, prevN = Mb[k], Nb[k]
+    rng = np.random.default_rng(seed)
+    qt = poisson_times(rate, horizon, rng)
+    qusers = [rng.integers(0, M_old, rng.integers(1, 17)).astype(np.int32) for _ in qt]
+    ut = [horizon * (k + 0.5) / n_inc for k in range(n_inc)]
+    events = sorted([(x, 0, q) for q, x in enumerate(qt)] + [(x, 1, k) for k, x in enumerate(ut)])
+    srv = Server(m, p, H, nbr, n=10, mode=1, max_users=4096)
+    # warm-up: a few queries of each size class and nothing else
+    for bs in (1, 16, 256):
+        srv.submit_topn(rng.integers(0, M_old, bs).astype(np.int32))
+    while srv.step():
+        pass
+    torch.cuda.synchronize()
+    srv.calls, srv.users_served = {"topn": 0, "ingest": 0}, 0
+    qreq, ureq = [], []
+
+    def produce():
+        t0 = time.perf_counter()
+        for x, kind, idx in events:
+            dt = t0 + x - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            if kind == 0:
+                qreq.append(srv.submit_topn(qusers[idx]))
+            else:
+                ureq.append(srv.submit_ingest(*incs[idx]))
+        srv.close()
+
+    th = threading.Thread(target=produce)
+    t0 = time.perf_counter()
+    th.start()
+    srv.serve_forever()
+    th.join()
+    wall = time.perf_counter() - t0
+    m.check()
+    out = {"what": "serve.Server: Poisson top-N queries (1-16 users, mode 1, top-10) + online updates",
+           "rate_per_s": rate, "horizon_s": horizon, "updates": n_inc,
+           "update_ratings": [int(len(x[2])) for x in incs],
+           "queries": latency_summary(qreq), "ingest": latency_summary(ureq),
+           "topn_calls": srv.calls["topn"], "mean_users_per_call": srv.users_served / max(1, srv.calls["topn"]),
+           "users_per_s": srv.users_served / wall, "wall_s": round(wall, 3)}
+    m.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -328,10 +412,11 @@ def run_ours(args, rank, world, local_rank):
     topn = None
     if rank == 0 and not args.no_serving:
         topn = measure_topn(m, p, w, dev)
-    ingest = None
+    ingest = serving = None
     if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
+        serving = measure_serving(w, d, P, dev)
 
     peak, peak_kind = peaks()
     ep_med = float(np.median(epoch_ms))
@@ -356,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
            "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
-           "topn": topn, "ingest": ingest,
+           "topn": topn, "ingest": ingest, "serving": serving,
            "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)

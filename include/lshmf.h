@@ -185,8 +185,11 @@ lshmf_status lshmf_train_strata(lshmf_handle *h, const lshmf_params *p, int32_t 
  * new users and items initialised by the caller; p->mu is the model's mean
  * (kept).  Requires lshmf_build_neighbours and lshmf_prepare_training of the
  * current model.  Afterwards the handle describes M + M_new users and N + N_new
- * items and its training layout is dropped: call lshmf_prepare_training with
- * all ratings before training or predicting again.  Synchronous. */
+ * items; its per-user rating lists and neighbour rows cover the increment, so
+ * lshmf_predict, lshmf_rmse and lshmf_topn serve the enlarged model at once,
+ * while the blocked layout of the SGD epoch is dropped (lshmf_train_epoch
+ * returns ESTATE until lshmf_prepare_training runs on all ratings).
+ * Synchronous. */
 lshmf_status lshmf_ingest(lshmf_handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
                           const int32_t *d_j, const uint8_t *d_r, int64_t n, const uint64_t *d_H,
                           int32_t *d_nbr, uint32_t *d_sig, const lshmf_params *p, int32_t local_epochs,

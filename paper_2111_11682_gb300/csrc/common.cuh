@@ -37,7 +37,8 @@ void release(DevBuf &b);
 
 // Training layout built by lshmf_prepare_training (all in blocked order).
 struct TrainLayout {
-  bool ready = false;
+  bool ready = false;     // the blocked layout of the SGD epoch matches the model
+  bool serving = false;   // user_ptr / csr_j / csr_r and nbr match the model (prediction, top-N)
   int64_t nnz = 0;
   int64_t nseg = 0;
   int64_t npacked = 0;

@@ -84,6 +84,34 @@ __global__ void k_ing_sums(const int64_t *ni_ptr, const int32_t *ni_i, const uin
   }
 }
 
+// Per-user rating lists of the enlarged model: the old list and the user's
+// part of the increment, both sorted by item, merged (one thread per user).
+__global__ void k_ing_merge_count(const int64_t *old_ptr, int64_t M, const int64_t *nu_ptr, int64_t Mt, int64_t *cnt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < Mt; i += int64_t(gridDim.x) * blockDim.x)
+    cnt[i] = (i < M ? old_ptr[i + 1] - old_ptr[i] : 0) + (nu_ptr[i + 1] - nu_ptr[i]);
+}
+__global__ void k_ing_merge(const int64_t *old_ptr, const int32_t *old_j, const uint8_t *old_r, int64_t M,
+                            const int64_t *nu_ptr, const int32_t *nu_j, const uint8_t *nu_r, int64_t Mt,
+                            const int64_t *mptr, int32_t *mj, uint8_t *mr) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < Mt; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t a = i < M ? old_ptr[i] : 0, ae = i < M ? old_ptr[i + 1] : 0;
+    int64_t b = nu_ptr[i], be = nu_ptr[i + 1], o = mptr[i];
+    while (a < ae || b < be) {
+      const bool take_a = b >= be || (a < ae && old_j[a] < nu_j[b]);
+      if (take_a) {
+        mj[o] = old_j[a];
+        mr[o] = old_r[a];
+        ++a;
+      } else {
+        mj[o] = nu_j[b];
+        mr[o] = nu_r[b];
+        ++b;
+      }
+      ++o;
+    }
+  }
+}
+
 __global__ void k_ing_copy_rows(const int32_t *src, int64_t first, int64_t nrows, int K, int32_t *dst) {
   const int64_t n = nrows * K;
   for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
@@ -363,7 +391,7 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   TrainLayout &tl = h->tl;
   const int64_t M = c.M, N = c.N, Mt = M + M_new, Nt = N + N_new;
   if (!S.ready || S.N != N) return set_err(h, LSHMF_ESTATE, "ingest: lshmf_build_neighbours has not run for this model");
-  if (!tl.ready) return set_err(h, LSHMF_ESTATE, "ingest: lshmf_prepare_training has not run for this model");
+  if (!tl.serving) return set_err(h, LSHMF_ESTATE, "ingest: lshmf_prepare_training has not run for this model");
   if (M_new < 0 || N_new < 0 || Mt >= (int64_t(1) << 31) || Nt >= (int64_t(1) << 31))
     return set_err(h, LSHMF_EINVAL, "ingest: bad new user/item counts");
   if (n < 0 || n >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "ingest: n out of range");
@@ -447,7 +475,8 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   a.inv_scale = 1.0f / c.rating_scale;
   a.M = M; a.N = N; a.Mt = Mt; a.Nt = Nt;
   a.F = c.F; a.K = c.K;
-  tl.ready = false;   // the training layout describes the model before the update
+  tl.ready = false;   // the blocked SGD layout describes the model before the update
+  tl.serving = false; // until the per-user lists are merged below
   const int fpl = (c.F + 31) / 32, kpl = (c.K + 31) / 32;
   lshmf_status s;
   if (fpl <= 1) s = kpl <= 1 ? run_local_sgd<1, 1>(h, a, epochs, st) : run_local_sgd<1, 2>(h, a, epochs, st);
@@ -455,6 +484,32 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   else if (fpl <= 4) s = kpl <= 1 ? run_local_sgd<4, 1>(h, a, epochs, st) : run_local_sgd<4, 2>(h, a, epochs, st);
   else s = kpl <= 1 ? run_local_sgd<8, 1>(h, a, epochs, st) : run_local_sgd<8, 2>(h, a, epochs, st);
   LSHMF_TRY(s);
+  // per-user lists and the neighbour rows of the enlarged model, for prediction and top-N
+  {
+    const int64_t n_old = tl.nnz;
+    DevBuf np, nj, nr;
+    LSHMF_TRY(ensure(h, np, sizeof(int64_t) * (Mt + 1) * 2, "ingest merged user lists"));
+    LSHMF_TRY(ensure(h, nj, sizeof(int32_t) * (n_old + n) + 64, "ingest merged user lists"));
+    LSHMF_TRY(ensure(h, nr, size_t(n_old + n) + 64, "ingest merged user lists"));
+    int64_t *cnt = np.as<int64_t>() + (Mt + 1);
+    const unsigned gm = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(Mt, 256), 16L * h->num_sms));
+    LSHMF_LAUNCH(h, k_ing_merge_count, gm, 256, 0, st, tl.user_ptr.as<int64_t>(), M, nu_ptr, Mt, cnt);
+    LSHMF_TRY(exclusive_scan_i64(h, cnt, np.as<int64_t>(), Mt, st));
+    LSHMF_LAUNCH(h, k_ing_merge, gm, 256, 0, st, tl.user_ptr.as<int64_t>(), tl.csr_j.as<int32_t>(),
+                 tl.csr_r.as<uint8_t>(), M, nu_ptr, nu_j, nu_r, Mt, np.as<int64_t>(), nj.as<int32_t>(),
+                 nr.as<uint8_t>());
+    LSHMF_CUDA(h, cudaStreamSynchronize(st));
+    std::swap(tl.user_ptr, np);
+    std::swap(tl.csr_j, nj);
+    std::swap(tl.csr_r, nr);
+    release(np);
+    release(nj);
+    release(nr);
+    LSHMF_TRY(ensure(h, tl.nbr, sizeof(int32_t) * Nt * c.K, "layout neighbours"));
+    LSHMF_CUDA(h, cudaMemcpyAsync(tl.nbr.p, d_nbr, sizeof(int32_t) * Nt * c.K, cudaMemcpyDeviceToDevice, st));
+    tl.nnz = n_old + n;
+    tl.serving = true;
+  }
   return check_device_flag(h, st, "ingest");
 }
 

@@ -459,7 +459,7 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
                   int32_t *d_items, float *d_scores, cudaStream_t st) {
   const lshmf_config &c = h->cfg;
   const TrainLayout &tl = h->tl;
-  if (!tl.ready) return set_err(h, LSHMF_ESTATE, "topn: lshmf_prepare_training has not succeeded");
+  if (!tl.serving) return set_err(h, LSHMF_ESTATE, "topn: lshmf_prepare_training has not succeeded");
   if (mode != 0 && mode != 1)
     return set_err(h, LSHMF_EINVAL, "topn: mode %d is not available (0 = FP32, 1 = BF16 candidates + FP32 rerank)", mode);
   if (c.N > TOPN_MAX_N) return set_err(h, LSHMF_EINVAL, "topn: N = %lld above %lld", (long long)c.N, (long long)TOPN_MAX_N);
@@ -495,9 +495,9 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
     t.Fp = (c.F + 15) & ~15;
     t.tiles = int((c.N + TC_N - 1) / TC_N);
     const int64_t utiles = (n + TC_M - 1) / TC_M;
-    // item slices: enough CTAs for two per SM, at most TC_MAX_SLICES
-    t.nslices = int(std::max<int64_t>(1, std::min<int64_t>({int64_t(TC_MAX_SLICES), int64_t(t.tiles),
-                                                            (2 * h->num_sms + utiles - 1) / utiles})));
+    // item slices: a function of N only, so that a user's candidates (and result) do not depend on the
+    // other users of the batch
+    t.nslices = int(std::min<int64_t>(TC_MAX_SLICES, t.tiles));
     t.tiles_per_slice = (t.tiles + t.nslices - 1) / t.nslices;
     t.nslices = (t.tiles + t.tiles_per_slice - 1) / t.tiles_per_slice;
     const int ncand = t.nslices * TC_C;

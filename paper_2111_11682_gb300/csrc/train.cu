@@ -319,6 +319,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   const int pbits = std::max(1, bits_for(NB));
   TrainLayout &tl = h->tl;
   tl.ready = false;
+  tl.serving = false;
   if (nnz <= 0) return set_err(h, LSHMF_EINVAL, "prepare_training: nnz must be positive");
   if (nnz >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "prepare_training: nnz >= 2^31");
   const bool wide = N > 32768;
@@ -495,6 +496,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   tl.max_users_per_block = int32_t(maxusers);
   tl.max_segs_per_block = int32_t(maxseg);
   tl.ready = true;
+  tl.serving = true;
   if (h_mu) *h_mu = mu;
   return LSHMF_OK;
 }
@@ -618,7 +620,7 @@ static PredArgs pred_args(Handle *h, const lshmf_params *p) {
 
 lshmf_status predict(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, int64_t n, float *out,
                      cudaStream_t st) {
-  if (!h->tl.ready) return set_err(h, LSHMF_ESTATE, "predict: lshmf_prepare_training has not succeeded");
+  if (!h->tl.serving) return set_err(h, LSHMF_ESTATE, "predict: lshmf_prepare_training has not succeeded");
   if (n == 0) return LSHMF_OK;
   LSHMF_LAUNCH(h, k_predict, grid_for(h, n, 8), 256, 0, st, pred_args(h, p), qi, qj, n, out);
   return LSHMF_OK;
@@ -628,7 +630,7 @@ constexpr int RMSE_CTAS = 1024;
 
 lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, const uint8_t *qr,
                   int64_t n, double *h_rmse, cudaStream_t st) {
-  if (!h->tl.ready) return set_err(h, LSHMF_ESTATE, "rmse: lshmf_prepare_training has not succeeded");
+  if (!h->tl.serving) return set_err(h, LSHMF_ESTATE, "rmse: lshmf_prepare_training has not succeeded");
   if (n <= 0) return set_err(h, LSHMF_EINVAL, "rmse: n must be positive");
   LSHMF_TRY(ensure(h, h->red_part, RMSE_CTAS * sizeof(double) + 64, "rmse partial sums"));
   double *part = h->red_part.as<double>();
@@ -647,7 +649,7 @@ lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int
 lshmf_status rmse_with_scratch(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj,
                                const uint8_t *qr, int64_t n, double *scratch, int64_t scratch_len, double *h_rmse,
                                cudaStream_t st) {
-  if (!h->tl.ready) return set_err(h, LSHMF_ESTATE, "rmse: lshmf_prepare_training has not succeeded");
+  if (!h->tl.serving) return set_err(h, LSHMF_ESTATE, "rmse: lshmf_prepare_training has not succeeded");
   if (n <= 0) return set_err(h, LSHMF_EINVAL, "rmse: n must be positive");
   const int64_t ctas = ceil_div(n, RMSE_PAIRS_PER_CTA);
   if (ctas + 1 > scratch_len) return set_err(h, LSHMF_EINVAL, "rmse: scratch too small");

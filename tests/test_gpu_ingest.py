@@ -103,9 +103,15 @@ def test_ingest_keys_rows_and_local_sgd(case):
     # old rows of the parameters are untouched
     assert np.array_equal(p.U[:M_old].cpu().numpy(), arrs[0][:M_old])
     assert np.array_equal(p.V[:N_old].cpu().numpy(), arrs[1][:N_old])
-    # the training layout was dropped: predictions need a new prepare
+    # prediction serves the enlarged model at once (per-user lists merged); training needs a new prepare
+    q = np.random.default_rng(4).choice(len(ni), 300, replace=False)
+    qi, qj = np.concatenate([ni[q], oi[:50]]), np.concatenate([nj[q], oj[:50]])
+    pred = m.predict(p, T(qi, torch.int32), T(qj, torch.int32)).cpu().numpy().astype(np.float64)
+    pg = oracle.Params(*(getattr(p, x).cpu().numpy().astype(np.float64) for x in ("U", "V", "b", "bh", "W", "C")))
+    pred_o = oracle.predict(cfg, d["train_i"], d["train_j"], d["train_r"], g, mu, pg, qi, qj)
+    assert np.abs(pred - pred_o).max() <= 1e-4 * (1 + np.abs(pred_o).max())
     with pytest.raises(LshmfError) as e:
-        m.predict(p, T(ni[:4], torch.int32), T(nj[:4], torch.int32))
+        m.train_epoch(p, 0)
     assert e.value.status == lshmf.ESTATE
     m.close()
 
@@ -131,11 +137,9 @@ def test_two_increments_equal_one_rebuild(case):
     p = _gpu_params(_params(w, M, N, 3), mu)
     m.ingest(150, 100, *(T(x, dt) for x, dt in zip(inc1, (torch.int32, torch.int32, torch.uint8))), H, nbr[:900],
              p, local_epochs=0)
-    # the second update needs the layout of the enlarged model
-    ui, uj, ur = np.concatenate([oi, inc1[0]]), np.concatenate([oj, inc1[1]]), np.concatenate([orr, inc1[2]])
-    m.prepare_training(T(ui, torch.int32), T(uj, torch.int32), T(ur, torch.uint8), nbr[:900].contiguous())
+    # the second update follows directly (it reads the per-user lists the first one merged)
     sig = m.ingest(M - 1850, N - 900, *(T(x, dt) for x, dt in zip(inc2, (torch.int32, torch.int32, torch.uint8))),
-                   H, nbr, p, local_epochs=0, want_sig=True)
+                   H, nbr, p, local_epochs=1, want_sig=True)
     torch.cuda.synchronize()
     sig_o = _oracle_sig(w, M, N, i, j, r, d["H"])
     assert np.array_equal(sig.cpu().numpy().view(np.uint32), sig_o)
