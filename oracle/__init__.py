@@ -64,6 +64,9 @@ def _load():
         "oracle_rmse": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, I64, P, P, P, P],
         "oracle_loss": [CP, I64, P, P, P, P, D, P, P, P, P, P, P, P],
         "oracle_mean": [I64, P, D],
+        "oracle_rand_rows": [I64, I32, ctypes.c_uint64, P],
+        "oracle_rpcos_signatures": [I64, I64, I32, I32, P, P, P, P, P],
+        "oracle_minhash_signatures": [I64, I64, I32, I32, I32, P, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -71,6 +74,8 @@ def _load():
         fn.restype = ctypes.c_int
     lib.oracle_rating_step.restype = ctypes.c_double
     lib.oracle_mean.restype = ctypes.c_double
+    lib.oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    lib.oracle_splitmix64.restype = ctypes.c_uint64
     _lib = lib
     return lib
 
@@ -115,6 +120,38 @@ def signatures(M, N, L, bits, psi_pow, col_ptr, row, r, H):
     col_ptr, row, r = _c(col_ptr, np.int64), _c(row, np.int32), _c(r, np.uint8)
     _check(_load().oracle_signatures(M, N, L, bits, psi_pow, _p(col_ptr), _p(row), _p(r), _p(H),
                                      H.shape[1], _p(out)), "signatures")
+    return out
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k >= 1 of the SplitMix64 sequence seeded with `seed`."""
+    return int(_load().oracle_splitmix64(seed, k))
+
+
+def rand_rows(N, K, seed):
+    """Random-neighbour rows (N, K) int32 (Sec. 5.3 "Rand")."""
+    out = np.zeros((N, K), dtype=np.int32)
+    _check(_load().oracle_rand_rows(N, K, seed, _p(out)), "rand_rows")
+    return out
+
+
+def rpcos_signatures(M, N, L, bits, col_ptr, row, r, A):
+    """RP_cos keys (L, N) uint32: sign of sum r_ij A[i, t bits + g] per bit (Sec. 5.3)."""
+    A = _c(A, np.int16)
+    out = np.zeros((L, N), dtype=np.uint32)
+    col_ptr, row, r = _c(col_ptr, np.int64), _c(row, np.int32), _c(r, np.uint8)
+    _check(_load().oracle_rpcos_signatures(M, N, L, bits, _p(col_ptr), _p(row), _p(r), _p(A), _p(out)),
+           "rpcos_signatures")
+    return out
+
+
+def minhash_signatures(M, N, L, bits, p, col_ptr, row, R):
+    """minHash keys (L, N) uint32: p sub-keys of bits/p low bits of per-table minima (Sec. 5.3)."""
+    R = _c(R, np.uint32)
+    out = np.zeros((L, N), dtype=np.uint32)
+    col_ptr, row = _c(col_ptr, np.int64), _c(row, np.int32)
+    _check(_load().oracle_minhash_signatures(M, N, L, bits, p, _p(col_ptr), _p(row), _p(R), _p(out)),
+           "minhash_signatures")
     return out
 
 

@@ -17,6 +17,9 @@
  *   oracle_topn                                 Eq. (1) top-N recommendation
  *   oracle_ingest_sgd                           Sec. 4.3, Alg. 4 local SGD of the
  *                                               online update
+ *   oracle_rand_rows / oracle_rpcos_signatures  Sec. 5.3, the top-K generators
+ *   / oracle_minhash_signatures                 compared with simLSH (Rand,
+ *                                               RP_cos, minHash)
  *
  * Readings of passages the paper leaves open (each is also listed in the
  * design notes):
@@ -693,4 +696,101 @@ double oracle_mean(int64_t nnz, const uint8_t *r, double rating_scale) {
   double s = 0.0;
   for (int64_t p = 0; p < nnz; ++p) s += (double)r[p];
   return s / (double)nnz / rating_scale;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 5.3: the other top-K generators the paper compares with simLSH. */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output number k >= 1 of
+ * the sequence whose state starts at `seed` (state advances by the golden
+ * gamma 0x9E3779B97F4A7C15, output = the 64-bit finaliser of the state). */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* Random neighbours ("Rand"): row j of J^K holds K distinct items other
+ * than j, drawn uniformly.  Draw t = 0, 1, ... of item j is output number
+ * j * 2^32 + t + 1 of one SplitMix64 sequence seeded with `seed`; its high
+ * 32 bits x give r = floor(x (N - 1) / 2^32) in [0, N - 1) and the
+ * candidate r + (r >= j); a candidate already in the row is skipped.  After
+ * 16 K + 256 draws a row still short is completed with the smallest unused
+ * items, in order. */
+int oracle_rand_rows(int64_t N, int32_t K, uint64_t seed, int32_t *nbr) {
+  if (K <= 0 || K > N - 1 || N > (1LL << 31) - 1) return ORC_EINVAL;
+  const int64_t T = 16LL * K + 256;
+  for (int64_t j = 0; j < N; ++j) {
+    int32_t *row = nbr + j * K;
+    int32_t n = 0;
+    for (int64_t t = 0; t < T && n < K; ++t) {
+      const uint64_t x = oracle_splitmix64(seed, ((uint64_t)j << 32) + (uint64_t)t + 1) >> 32;
+      const int64_t r = (int64_t)((x * (uint64_t)(N - 1)) >> 32);
+      const int32_t cand = (int32_t)(r + (r >= j));
+      int dup = 0;
+      for (int32_t q = 0; q < n; ++q) dup |= row[q] == cand;
+      if (!dup) row[n++] = cand;
+    }
+    for (int64_t q = 0; q < N && n < K; ++q) {
+      if (q == j) continue;
+      int dup = 0;
+      for (int32_t s = 0; s < n; ++s) dup |= row[s] == q;
+      if (!dup) row[n++] = (int32_t)q;
+    }
+  }
+  return ORC_OK;
+}
+
+/* RP_cos: random-hyperplane LSH of the item columns (sign random
+ * projections, cosine similarity).  Bit g of table t of item j is 1 iff
+ * sum over raters i of r_ij * A[i * (L bits) + t bits + g] >= 0, A the
+ * integer Gaussian projection coefficients (int16, drawn by the caller). */
+int oracle_rpcos_signatures(int64_t M, int64_t N, int32_t L, int32_t bits, const int64_t *col_ptr,
+                            const int32_t *row, const uint8_t *r, const int16_t *A, uint32_t *sig) {
+  if (L <= 0 || bits <= 0 || bits > 32) return ORC_EINVAL;
+  const int64_t LB = (int64_t)L * bits;
+  for (int64_t j = 0; j < N; ++j)
+    for (int32_t t = 0; t < L; ++t) {
+      uint32_t key = 0;
+      for (int32_t g = 0; g < bits; ++g) {
+        int64_t s = 0;
+        for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) {
+          if (row[p] < 0 || row[p] >= M) return ORC_EINVAL;
+          s += (int64_t)r[p] * (int64_t)A[(int64_t)row[p] * LB + (int64_t)t * bits + g];
+        }
+        if (s >= 0) key |= 1u << g;
+      }
+      sig[(int64_t)t * N + j] = key;
+    }
+  return ORC_OK;
+}
+
+/* minHash: table t's key of item j concatenates p sub-keys of G = bits / p
+ * bits; sub-key k is the low G bits of the minimum over raters i of
+ * R[i * (L p) + t p + k] (uint32 random values drawn per user by the caller,
+ * standing in for a random permutation of the users).  An item with no
+ * raters takes the minimum 2^32 - 1.  Sub-key k sits at bits [k G, (k+1) G). */
+int oracle_minhash_signatures(int64_t M, int64_t N, int32_t L, int32_t bits, int32_t p,
+                              const int64_t *col_ptr, const int32_t *row, const uint32_t *R, uint32_t *sig) {
+  if (L <= 0 || bits <= 0 || bits > 32 || p <= 0 || bits % p) return ORC_EINVAL;
+  const int32_t G = bits / p;
+  const int64_t Lp = (int64_t)L * p;
+  for (int64_t j = 0; j < N; ++j)
+    for (int32_t t = 0; t < L; ++t) {
+      uint32_t key = 0;
+      for (int32_t k = 0; k < p; ++k) {
+        uint32_t m = 0xFFFFFFFFu;
+        for (int64_t q = col_ptr[j]; q < col_ptr[j + 1]; ++q) {
+          if (row[q] < 0 || row[q] >= M) return ORC_EINVAL;
+          const uint32_t v = R[(int64_t)row[q] * Lp + (int64_t)t * p + k];
+          if (v < m) m = v;
+        }
+        const uint32_t low = G == 32 ? m : (m & ((1u << G) - 1u));
+        key |= low << (k * G);
+      }
+      sig[(int64_t)t * N + j] = key;
+    }
+  return ORC_OK;
 }
