@@ -306,6 +306,51 @@ def measure_serving(w, d, P, dev, frac=0.01, n_inc=4, rate=4000.0, horizon=2.0, 
     return out
 
 
+def measure_generators(w, d, P, dev, reps=3):
+    """Neighbour build time of each top-K generator the paper compares (Sec. 5.3 time-overhead
+    table): simLSH (lshmf_build_neighbours) and Rand, RP_cos, minHash (p = 3 sub-keys per table)
+    through lshmf_build_neighbours_variant, on the workload's CSC (built untimed).  CUDA events
+    around one call, median of `reps` after one warm-up."""
+    import torch
+
+    import synth
+    from paper_2111_11682_gb300 import LshMF, config_from_workload, lshmf
+
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    m = LshMF(config_from_workload(w, P))
+    col_ptr, row, rc = m.csc_from_coo(t(d["train_i"], torch.int32), t(d["train_j"], torch.int32),
+                                      t(d["train_r"], torch.uint8))
+    H = t(d["H"].view(np.int64), torch.int64)
+    A = t(synth.projections_i16(w.M, w.L * w.bits, 41), torch.int16)
+    p_mh = 3 if w.bits % 3 == 0 else 1
+    R = t(synth.random_u32(w.M, w.L * p_mh, 43).view(np.int32), torch.int32)
+    nbr = torch.empty((w.N, w.K), dtype=torch.int32, device=dev)
+    calls = {
+        "simLSH": lambda: m.build_neighbours(col_ptr, row, rc, H, nbr_out=nbr),
+        "Rand": lambda: m.build_neighbours_variant(lshmf.GEN_RAND, seed=5, nbr_out=nbr, device=dev),
+        "RP_cos": lambda: m.build_neighbours_variant(lshmf.GEN_RPCOS, col_ptr, row, rc, A, nbr_out=nbr),
+        "minHash (p=%d)" % p_mh: lambda: m.build_neighbours_variant(lshmf.GEN_MINHASH, col_ptr, row, rc, R, p=p_mh,
+                                                                   nbr_out=nbr),
+    }
+    out = {"what": "neighbour build per top-K generator (keys + buckets + top-K rows), ms",
+           "L": w.L, "bits": w.bits, "K": w.K, "ms_median": {}}
+    for name, fn in calls.items():
+        ms = []
+        for k in range(reps + 1):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if k > 0:
+                ms.append(a.elapsed_time(b))
+        out["ms_median"][name] = round(float(np.median(ms)), 3)
+    m.check()
+    m.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -412,11 +457,12 @@ def run_ours(args, rank, world, local_rank):
     topn = None
     if rank == 0 and not args.no_serving:
         topn = measure_topn(m, p, w, dev)
-    ingest = serving = None
+    ingest = serving = generators = None
     if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
         serving = measure_serving(w, d, P, dev)
+        generators = measure_generators(w, d, P, dev)
 
     peak, peak_kind = peaks()
     ep_med = float(np.median(epoch_ms))
@@ -441,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
            "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
-           "topn": topn, "ingest": ingest, "serving": serving,
+           "topn": topn, "ingest": ingest, "serving": serving, "generators": generators,
            "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)

@@ -129,6 +129,42 @@ lshmf_status lshmf_build_neighbours(lshmf_handle *h, const int64_t *d_col_ptr, c
                                     const uint8_t *d_rc, int64_t nnz, const uint64_t *d_H,
                                     int32_t *d_nbr, uint32_t *d_sig, void *stream);
 
+/* Top-K generators the paper compares with simLSH (Sec. 5.3, table of the
+ * optimal RMSE and overhead of the top-K methods).  `generator` selects:
+ *
+ *   LSHMF_GEN_RAND     random neighbours: row j holds K distinct items other
+ *       than j.  Draw t = 0, 1, ... of item j is output number
+ *       j * 2^32 + t + 1 of the SplitMix64 sequence (Steele, Lea and Flood
+ *       2014) seeded with `seed`; its high 32 bits x give
+ *       r = floor(x (N - 1) / 2^32) and the candidate r + (r >= j); repeats
+ *       are skipped; after 16 K + 256 draws a short row is completed with
+ *       the smallest unused items.  The CSC and d_rand are not read (may be
+ *       NULL); d_sig must be NULL.
+ *   LSHMF_GEN_RPCOS    random-hyperplane LSH (cosine): bit g of table t of
+ *       item j is [sum over raters i of r_ij * A[i][t * bits + g] >= 0];
+ *       d_rand = A, int16 [M x (L * bits)] projection coefficients (integer
+ *       Gaussian draws by the caller).  Sums are exact (int64).
+ *   LSHMF_GEN_MINHASH  minHash (Jaccard): table t's key concatenates p
+ *       sub-keys of G = bits / p bits; sub-key k (bits [k G, (k+1) G)) is the
+ *       low G bits of min over raters i of R[i][t * p + k]; d_rand = R,
+ *       uint32 [M x (L * p)] random values per user.  An item with no raters
+ *       takes the minimum 2^32 - 1.  Needs 1 <= p <= bits, bits % p == 0.
+ *
+ * RP_cos and minHash keys go through the same buckets and top-K search as
+ * lshmf_build_neighbours (rows in (count desc, item asc) order, cnt = 0
+ * items in index order); d_sig [L x N] receives the keys, or NULL.  The CSC
+ * is validated as in lshmf_build_neighbours (EINVAL).  A handle whose
+ * neighbours came from a variant has no kept simLSH sums: lshmf_ingest
+ * returns LSHMF_ESTATE until the next lshmf_build_neighbours.
+ * Asynchronous except for the CSC check. */
+#define LSHMF_GEN_RAND 1
+#define LSHMF_GEN_RPCOS 2
+#define LSHMF_GEN_MINHASH 3
+lshmf_status lshmf_build_neighbours_variant(lshmf_handle *h, int32_t generator, const int64_t *d_col_ptr,
+                                            const int32_t *d_row, const uint8_t *d_rc, int64_t nnz,
+                                            const void *d_rand, int32_t p, uint64_t seed, int32_t *d_nbr,
+                                            uint32_t *d_sig, void *stream);
+
 /* Training layout, Sec. 4.2.  Sorts the training triples (any order, no
  * duplicates) into the P x P blocks of the stratified schedule (user block
  * floor(i P / M), item block floor(j P / N); inside a block (j asc, i asc)),

@@ -7,6 +7,9 @@ lshmf_status csc_from_coo(Handle *h, const int32_t *d_i, const int32_t *d_j, con
                           int64_t *col_ptr, int32_t *row, uint8_t *rc, cudaStream_t st);
 lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc,
                               int64_t nnz, const uint64_t *H, int32_t *nbr, uint32_t *sig_out, cudaStream_t st);
+lshmf_status build_neighbours_variant(Handle *h, int32_t gen, const int64_t *col_ptr, const int32_t *row,
+                                      const uint8_t *rc, int64_t nnz, const void *rnd, int32_t p, uint64_t seed,
+                                      int32_t *nbr, uint32_t *sig_out, cudaStream_t st);
 lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r, int64_t nnz,
                               const int32_t *d_nbr, double *h_mu, cudaStream_t st);
 lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
@@ -130,6 +133,31 @@ lshmf_status lshmf_build_neighbours(lshmf_handle *hh, const int64_t *d_col_ptr, 
   if (!d_col_ptr || !d_H || !d_nbr || (nnz > 0 && (!d_row || !d_rc)))
     return set_err(h, LSHMF_EINVAL, "build_neighbours: null pointer");
   return build_neighbours(h, d_col_ptr, d_row, d_rc, nnz, d_H, d_nbr, d_sig, S(stream));
+}
+
+lshmf_status lshmf_build_neighbours_variant(lshmf_handle *hh, int32_t generator, const int64_t *d_col_ptr,
+                                            const int32_t *d_row, const uint8_t *d_rc, int64_t nnz,
+                                            const void *d_rand, int32_t p, uint64_t seed, int32_t *d_nbr,
+                                            uint32_t *d_sig, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  const lshmf_config &c = h->cfg;
+  if (generator != LSHMF_GEN_RAND && generator != LSHMF_GEN_RPCOS && generator != LSHMF_GEN_MINHASH)
+    return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: unknown generator %d", generator);
+  if (!d_nbr) return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: null pointer");
+  if (generator == LSHMF_GEN_RAND) {
+    if (d_sig) return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: random neighbours have no keys");
+    return build_neighbours_variant(h, generator, nullptr, nullptr, nullptr, 0, nullptr, 0, seed, d_nbr, nullptr,
+                                    S(stream));
+  }
+  if (nnz < 0 || nnz >= (int64_t(1) << 31))
+    return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: nnz out of range");
+  if (!d_col_ptr || !d_rand || (nnz > 0 && (!d_row || !d_rc)))
+    return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: null pointer");
+  if (generator == LSHMF_GEN_MINHASH && (p < 1 || p > c.bits || c.bits % p != 0))
+    return set_err(h, LSHMF_EINVAL, "build_neighbours_variant: minHash needs 1 <= p <= bits and bits %% p == 0");
+  return build_neighbours_variant(h, generator, d_col_ptr, d_row, d_rc, nnz, d_rand, p, seed, d_nbr, d_sig,
+                                  S(stream));
 }
 
 lshmf_status lshmf_prepare_training(lshmf_handle *hh, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r,

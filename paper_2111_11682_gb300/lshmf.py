@@ -21,7 +21,9 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
-           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc"]
+           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant"]
+
+GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
 
 
 class LshmfError(RuntimeError):
@@ -90,6 +92,7 @@ def load(build_if_missing: bool = True):
         "lshmf_launch_count": ([], I64),
         "lshmf_csc_from_coo": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
         "lshmf_build_neighbours": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+        "lshmf_build_neighbours_variant": ([P, I32, P, P, P, I64, P, I32, ctypes.c_uint64, P, P, P], ctypes.c_int),
         "lshmf_prepare_training": ([P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_train_epoch": ([P, CP, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_train_strata": ([P, CP, I32, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
@@ -210,6 +213,19 @@ class LshMF:
                                                   _ptr(nbr), _ptr(sig), _stream(stream)))
         return (nbr, sig) if want_sig else nbr
 
+    def build_neighbours_variant(self, generator, col_ptr=None, row=None, rc=None, rand=None, p=0, seed=0,
+                                 want_sig=False, nbr_out=None, device="cuda", stream=None):
+        """lshmf_build_neighbours_variant: GEN_RAND (seed), GEN_RPCOS (rand = int16 [M, L*bits]) or
+        GEN_MINHASH (rand = int32 view of uint32 [M, L*p], p sub-keys per table)."""
+        c = self.cfg
+        dev = row.device if row is not None else torch.device(device)
+        nbr = nbr_out if nbr_out is not None else torch.empty((c.N, c.K), dtype=torch.int32, device=dev)
+        sig = torch.empty((c.L, c.N), dtype=torch.int32, device=dev) if want_sig else None
+        nnz = row.numel() if row is not None else 0
+        self._chk(self.lib.lshmf_build_neighbours_variant(self.h, generator, _ptr(col_ptr), _ptr(row), _ptr(rc), nnz,
+                                                          _ptr(rand), p, seed, _ptr(nbr), _ptr(sig), _stream(stream)))
+        return (nbr, sig) if want_sig else nbr
+
     def prepare_training(self, i, j, r, nbr, stream=None) -> float:
         mu = ctypes.c_double(0.0)
         self._chk(self.lib.lshmf_prepare_training(self.h, _ptr(i), _ptr(j), _ptr(r), i.numel(), _ptr(nbr),
@@ -279,6 +295,19 @@ class LshMF:
         self._chk(self.lib.lshmf_rmse_noalloc(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), _ptr(r),
                                               users.numel(), ctypes.byref(out), _stream(stream)))
         return out.value
+
+
+def plain_mf_config(cfg: Config) -> Config:
+    """The configuration under which the model of Eq. (1) is plain MF (CUSGD++, Alg. 2): learning
+    rates and regularisers of b, bhat, w and c set to 0.  With parameters b = bhat = W = C = 0 and
+    mu = 0 every neighbour and bias term is an exact zero, so lshmf_train_epoch runs textbook MF SGD
+    (r_hat = u . v) over the same stratified schedule."""
+    c = Config.make(cfg.M, cfg.N, cfg.F, cfg.K, cfg.L, cfg.bits, cfg.psi_pow, cfg.P, list(cfg.alpha), cfg.beta,
+                    list(cfg.lambda_), cfg.rating_scale)
+    for g in (0, 1, 4, 5):
+        c.alpha[g] = 0.0
+        c.lambda_[g] = 0.0
+    return c
 
 
 def config_from_workload(w, P=None) -> Config:

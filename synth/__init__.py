@@ -182,3 +182,18 @@ def shuffled(d: dict, seed: int = 1) -> dict:
     out = dict(d)
     out["train_i"], out["train_j"], out["train_r"] = d["train_i"][p], d["train_j"][p], d["train_r"][p]
     return out
+
+
+def projections_i16(M: int, cols: int, seed: int) -> np.ndarray:
+    """Integer Gaussian projection coefficients for the RP_cos generator: round(4096 N(0, 1)),
+    clipped to int16, shape (M, cols) (the random hyperplanes RP_cos draws per user)."""
+    z = np.empty(M * cols, dtype=np.float32)
+    _load().synth_normal_f32(z.size, seed & (2**64 - 1), 4096.0, _ptr(z))
+    return np.clip(np.rint(z), -32767, 32767).astype(np.int16).reshape(M, cols)
+
+
+def random_u32(M: int, cols: int, seed: int) -> np.ndarray:
+    """Uniform 32-bit random values per user for the minHash generator, shape (M, cols)."""
+    W = (cols + 1) // 2
+    H = hash_bits(M, W, seed)
+    return np.ascontiguousarray(H.view(np.uint32)[:, :cols])

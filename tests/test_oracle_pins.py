@@ -471,3 +471,32 @@ def test_topk_rows_equal_bruteforce():
     full = oracle.topk_bruteforce(sig, 7)
     rows = np.array([0, 13, 59, 27], dtype=np.int32)
     assert np.array_equal(oracle.topk_rows(sig, 7, rows), full[rows])
+
+
+@pytest.mark.parametrize("P", [1, 3])
+def test_plain_mf_special_case_is_textbook_sgd(P):
+    """CUSGD++ (Alg. 2) trains plain MF: r_hat = u_i . v_j, e = r - r_hat, u <- u + g(e v - l u),
+    v <- v + g(e u - l v).  The model of Eq. (1) with W = C = 0, b = bhat = 0, mu = 0 and zero
+    learning rates for b, bhat, w, c is exactly that model; its epoch equals textbook MF SGD
+    written out here over the same stratum order."""
+    rng = np.random.default_rng(10 + P)
+    M, N, F, K = 11, 8, 4, 3
+    pairs = [(i, j) for i in range(M) for j in range(N) if rng.random() < 0.5]
+    rng.shuffle(pairs)
+    ti = np.array([p[0] for p in pairs], dtype=np.int32)
+    tj = np.array([p[1] for p in pairs], dtype=np.int32)
+    tr = rng.integers(1, 6, len(pairs)).astype(np.uint8)
+    nbr = np.array([rng.permutation([q for q in range(N) if q != j])[:K] for j in range(N)], dtype=np.int32)
+    U0, V0 = rng.normal(0, .3, (M, F)), rng.normal(0, .3, (N, F))
+    prm = oracle.Params(U0.copy(), V0.copy(), np.zeros(M), np.zeros(N), np.zeros((N, K)), np.zeros((N, K)))
+    g, l, beta, epoch = 0.03, 0.05, 0.3, 1
+    cfg = oracle.make_cfg(M, N, F, K, P, (0, 0, g, g, 0, 0), beta, (0, 0, l, l, 0, 0))
+    oracle.train(cfg, ti, tj, tr, nbr, 0.0, prm, epoch)
+    U, V = U0.copy(), V0.copy()
+    gt = g / (1 + beta * epoch ** 1.5)
+    for p in _python_schedule(M, N, P, ti, tj):
+        i, j = int(ti[p]), int(tj[p])
+        e = float(tr[p]) - U[i] @ V[j]
+        U[i], V[j] = U[i] + gt * (e * V[j] - l * U[i]), V[j] + gt * (e * U[i] - l * V[j])
+    assert np.allclose(prm.U, U, rtol=0, atol=1e-12) and np.allclose(prm.V, V, rtol=0, atol=1e-12)
+    assert not prm.b.any() and not prm.bh.any() and not prm.W.any() and not prm.C.any()
