@@ -15,6 +15,7 @@ Multi-GPU: replicas only (one independent job per rank), weak scaling.
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -351,6 +352,112 @@ def measure_generators(w, d, P, dev, reps=3):
     return out
 
 
+def measure_batch(dev, n_inst=256, E=3, seed=7):
+    """Many small independent models trained together: `n_inst` uneven instances (users 1k-40k and
+    items 300-4k log-uniform, density 0.5-3 %, at most 600k ratings; F = K = 32, L = 8, bits = 8),
+    simLSH neighbours, P of each chosen by the autotuner (least SM-time per epoch among 4..64, the
+    fastest P for instances that would otherwise be the batch's critical path).
+    Times E epochs of every instance (CUDA events around the whole job, parameters reset untimed):
+    per-instance lshmf_train_epoch calls from a host loop, against one CUDA graph of the whole job
+    (lshmf_batch) with instances on 1 or more parallel branches, round-robin or longest-first by the
+    autotuner's epoch time."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    from paper_2111_11682_gb300 import (Batch, Config, LshMF, Params, autotune_P, config_from_workload,
+                                        plan_batch_P)
+
+    rng = np.random.default_rng(seed)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    models, inits, nnz_all, timings, data, t0 = [], [], [], [], [], time.time()
+    for x in range(n_inst):
+        M = int(np.exp(rng.uniform(np.log(1000), np.log(40000))))
+        N = int(np.exp(rng.uniform(np.log(300), np.log(4000))))
+        nnz = int(min(600_000, max(2000, M * N * rng.uniform(0.005, 0.03))))
+        w = dataclasses.replace(synth.TINY, name=f"inst{x}", M=M, N=N, nnz=nnz, F=32, K=32, L=8, bits=8,
+                                beta=0.3, seed=1000 + x, test_frac=0.0)
+        d = synth.generate(w)
+        m0 = LshMF(config_from_workload(w))
+        ti, tj, tr = t(d["train_i"], torch.int32), t(d["train_j"], torch.int32), t(d["train_r"], torch.uint8)
+        col_ptr, row, rc = m0.csc_from_coo(ti, tj, tr)
+        nbr = m0.build_neighbours(col_ptr, row, rc, t(d["H"].view(np.int64), torch.int64))
+        p0 = Params.from_init(d["U0"], d["V0"], w.K, dev)
+        m, mu, tim = autotune_P(m0.cfg, ti, tj, tr, nbr, p0, candidates=(4, 8, 16, 32, 64), reps=1)
+        m0.close()
+        p0.mu = mu
+        timings.append(tim)
+        data.append((ti, tj, tr, nbr))
+        models.append(m)
+        inits.append(p0)
+        nnz_all.append(len(d["train_i"]))
+    # P per instance for the batch: least SM-time, except instances that would be the critical path
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    plan = plan_batch_P(timings, E, sms)
+    moved = 0
+    for x, P in enumerate(plan):
+        if P != models[x].cfg.P:
+            c = models[x].cfg
+            m = LshMF(Config.make(c.M, c.N, c.F, c.K, c.L, c.bits, c.psi_pow, P, list(c.alpha), c.beta,
+                                  list(c.lambda_), c.rating_scale))
+            m.prepare_training(*data[x])
+            models[x].close()
+            models[x] = m
+            moved += 1
+    costs = [timings[x][plan[x]] for x in range(n_inst)]
+    del data
+    setup_s = time.time() - t0
+    ps = [p.clone() for p in inits]
+
+    def reset():
+        for q, p in zip(ps, inits):
+            q.copy_(p)
+        torch.cuda.synchronize()
+
+    def timed(fn, reps=3):
+        ms = []
+        for _ in range(reps):
+            reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    def eager():
+        for e in range(E):
+            for m, q in zip(models, ps):
+                m.train_epoch(q, e)
+
+    total = float(sum(nnz_all)) * E
+    out = {"what": "%d uneven instances x %d epochs: host loop of lshmf_train_epoch vs one CUDA graph "
+                   "(lshmf_batch)" % (n_inst, E),
+           "instances": n_inst, "ratings": int(sum(nnz_all)), "epochs": E,
+           "P_histogram": {str(k): int(v) for k, v in zip(*np.unique([m.cfg.P for m in models], return_counts=True))},
+           "moved_to_fastest_P": moved, "setup_s": round(setup_s, 1), "modes": {}}
+    timed(eager, reps=1)
+    ms = timed(eager)
+    out["modes"]["per_instance_calls"] = {"ms": round(ms, 2), "rating_updates_per_s": total / (ms / 1e3)}
+    ref = [q.clone() for q in ps]
+    fill = int(math.ceil(sms / np.mean([min(m.cfg.P, sms) for m in models])))   # branches that fill the SMs
+    for nb, cost in ((1, None), (32, None), (fill, costs), (2 * fill, costs)):
+        b = Batch(models, ps, epoch0=0, epochs=E, branches=nb, cost=cost)
+        timed(b.run, reps=1)
+        ms = timed(b.run)
+        b.check()
+        same = all(torch.equal(getattr(q, n), getattr(r, n)) for q, r in zip(ps, ref) for n in ("U", "V", "W"))
+        name = "graph_%d_branches_%s" % (nb, "round_robin" if cost is None else "longest_first")
+        out["modes"][name] = {"ms": round(ms, 2), "rating_updates_per_s": total / (ms / 1e3),
+                              "kernels": b.kernels, "equal_to_per_instance": bool(same)}
+        b.close()
+    for m in models:
+        m.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -457,12 +564,13 @@ def run_ours(args, rank, world, local_rank):
     topn = None
     if rank == 0 and not args.no_serving:
         topn = measure_topn(m, p, w, dev)
-    ingest = serving = generators = None
+    ingest = serving = generators = batch = None
     if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
         serving = measure_serving(w, d, P, dev)
         generators = measure_generators(w, d, P, dev)
+        batch = measure_batch(dev)
 
     peak, peak_kind = peaks()
     ep_med = float(np.median(epoch_ms))
@@ -487,7 +595,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
            "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
-           "topn": topn, "ingest": ingest, "serving": serving, "generators": generators,
+           "topn": topn, "ingest": ingest, "serving": serving, "generators": generators, "batch": batch,
            "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)

@@ -298,6 +298,48 @@ lshmf_status lshmf_rmse_noalloc(lshmf_handle *h, const lshmf_params *p, const in
                                 const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,
                                 void *stream);
 
+/* Batched training of many independent models as one CUDA graph (no
+ * counterpart in the paper, which trains one model at a time).
+ * Instance x is handles[x] (prepared; its own configuration and P) with
+ * parameters params[x].  lshmf_batch_create records, by stream capture, the
+ * launches that lshmf_train_epoch(handles[x], &params[x], e) issues for
+ * e = epoch0 .. epoch0 + epochs - 1, for every instance, instances spread
+ * over `branches` parallel branches of the graph (1 = one after another):
+ * round-robin if cost is NULL, else longest first (instances in decreasing
+ * cost[x] >= 0, each to the branch with the least total cost so far, ties
+ * to the lower branch; inside a branch in that order); no kernel runs during the call apart from a pre-flight that
+ * only refreshes each instance's epoch-start scratch.  The launches, and so
+ * each instance's result, are those of the separate calls: a run of the
+ * batch leaves every instance's parameters bit-identical to training it
+ * alone.  The handles and the parameter arrays must outlive the batch, keep
+ * their prepared layout, and not be used by other calls while a run is in
+ * flight.  n >= 1, epochs >= 1, branches >= 1, costs >= 0, no handle listed
+ * twice (EINVAL).  *out is NULL on failure. */
+typedef struct lshmf_batch lshmf_batch;
+lshmf_status lshmf_batch_create(lshmf_handle *const *handles, const lshmf_params *params, const double *cost,
+                                int32_t n, int32_t epoch0, int32_t epochs, int32_t branches, lshmf_batch **out);
+
+/* The assignment lshmf_batch_create uses (host only, no GPU needed):
+ * branch_of[x] = branch of instance x, order = instances in capture order,
+ * for min(branches, n) branches.  cost NULL: round-robin in index order;
+ * else longest first as described above.  EINVAL on n < 1, branches < 1,
+ * a negative or NaN cost, or a NULL output. */
+lshmf_status lshmf_batch_plan(const double *cost, int32_t n, int32_t branches, int32_t *branch_of,
+                              int32_t *order);
+
+/* Launches the batch's graph on `stream` (asynchronous). */
+lshmf_status lshmf_batch_run(lshmf_batch *b, void *stream);
+
+/* Synchronises `stream` and returns the first device-side error recorded by
+ * any instance (as lshmf_check), or LSHMF_OK. */
+lshmf_status lshmf_batch_check(lshmf_batch *b, void *stream);
+
+/* Kernel launches in one run of the batch (graph kernel nodes); -1 for NULL. */
+int64_t lshmf_batch_kernels(const lshmf_batch *b);
+
+/* Frees the graph (the handles are not touched). */
+void lshmf_batch_destroy(lshmf_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liblshmf.so")
-SOURCES = ["abi.cu", "sort.cu", "simlsh.cu", "variants.cu", "train.cu", "sgd.cu", "ingest.cu", "topn.cu", "noalloc.cu"]
+SOURCES = ["abi.cu", "sort.cu", "simlsh.cu", "variants.cu", "train.cu", "sgd.cu", "ingest.cu", "topn.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -921,7 +921,11 @@ static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream
   a.nslots = ns;
   a.cqn = ns * maxseg;
   const size_t smem = need(ng, ns);
-  LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_stratum<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the attribute is a per-kernel cap shared by every handle: set it to the device maximum so that
+  // launches of handles with different block sizes (captured together into one graph, or issued from
+  // several threads) never see another handle's smaller cap
+  LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_stratum<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     h->smem_optin));
   const int grid = std::min(h->num_sms, a.P);
   for (int s = 0; s < n_strata; ++s)
     LSHMF_LAUNCH(h, (k_sgd_stratum<FPL, KPL>), grid, 32 * (ng * (GP + 1) + 1), smem, st, a, s, ng);

@@ -21,7 +21,8 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
-           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant"]
+           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant",
+           "lshmf_batch_create", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
 
 GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
 
@@ -102,6 +103,12 @@ def load(build_if_missing: bool = True):
         "lshmf_rmse_noalloc": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_ingest": ([P, I64, I64, P, P, P, I64, P, P, P, CP, I32, P], ctypes.c_int),
         "lshmf_topn": ([P, CP, P, I64, I32, I32, P, P, P], ctypes.c_int),
+        "lshmf_batch_create": ([P, CP, P, I32, I32, I32, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "lshmf_batch_plan": ([P, I32, I32, P, P], ctypes.c_int),
+        "lshmf_batch_run": ([P, P], ctypes.c_int),
+        "lshmf_batch_check": ([P, P], ctypes.c_int),
+        "lshmf_batch_kernels": ([P], I64),
+        "lshmf_batch_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +302,144 @@ class LshMF:
         self._chk(self.lib.lshmf_rmse_noalloc(self.h, ctypes.byref(cp), _ptr(users), _ptr(items), _ptr(r),
                                               users.numel(), ctypes.byref(out), _stream(stream)))
         return out.value
+
+
+class Batch:
+    """lshmf_batch_*: epochs [epoch0, epoch0 + epochs) of every (model, params) pair recorded as one
+    CUDA graph, instances over `branches` parallel branches (round-robin, or longest-first by `cost`).  Keeps references to the
+    models and parameter tensors (they must stay alive and unchanged in shape while the batch lives)."""
+
+    def __init__(self, models, params, epoch0=0, epochs=1, branches=1, cost=None):
+        if len(models) != len(params) or not models or (cost is not None and len(cost) != len(models)):
+            raise ValueError("Batch: need one Params (and one cost, if given) per model")
+        self.lib = load()
+        self.models, self.params = list(models), list(params)
+        hs = (ctypes.c_void_p * len(models))(*(m.h.value for m in models))
+        self._cp = (_CParams * len(params))(*(p._c() for p in params))
+        cst = (ctypes.c_double * len(cost))(*map(float, cost)) if cost is not None else None
+        b = ctypes.c_void_p()
+        st = self.lib.lshmf_batch_create(hs, self._cp, cst, len(models), epoch0, epochs, branches, ctypes.byref(b))
+        if st != OK:
+            msgs = "; ".join(m.lib.lshmf_last_error(m.h).decode() for m in models if m.lib.lshmf_last_error(m.h))
+            raise LshmfError(st, "lshmf_batch_create failed" + (f" ({msgs})" if msgs else ""))
+        self.b = b
+
+    @property
+    def kernels(self) -> int:
+        return int(self.lib.lshmf_batch_kernels(self.b))
+
+    def run(self, stream=None):
+        st = self.lib.lshmf_batch_run(self.b, _stream(stream))
+        if st != OK:
+            raise LshmfError(st, "lshmf_batch_run failed")
+
+    def check(self, stream=None):
+        st = self.lib.lshmf_batch_check(self.b, _stream(stream))
+        if st != OK:
+            msgs = "; ".join(m.lib.lshmf_last_error(m.h).decode() for m in self.models if m.lib.lshmf_last_error(m.h))
+            raise LshmfError(st, "batch: " + msgs)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.lshmf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_plan(cost, branches):
+    """lshmf_batch_plan (host only): (branch of each instance, capture order) for a cost list, or
+    round-robin for cost = an int n (number of instances)."""
+    import numpy as np
+
+    lib = load(build_if_missing=False)
+    n = cost if isinstance(cost, int) else len(cost)
+    bo, order = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    c = None if isinstance(cost, int) else np.ascontiguousarray(cost, np.float64)
+    st = lib.lshmf_batch_plan(None if c is None else c.ctypes.data, n, branches, bo.ctypes.data, order.ctypes.data)
+    if st != OK:
+        raise LshmfError(st, "lshmf_batch_plan")
+    return bo, order
+
+
+def pick_P(timings: dict, objective: str = "sm_time", num_sms: int = 152) -> int:
+    """Choice of the autotuner: timings maps P -> measured epoch ms (None where the layout did not
+    fit).  "latency": the fastest epoch alone.  "sm_time": the least SM-time, epoch ms x min(P, SMs)
+    (a stratum launch occupies min(P, SMs) SMs), the cost that matters when many instances share the
+    GPU.  Ties go to the smaller P."""
+    ok = {P: t for P, t in timings.items() if t is not None}
+    if not ok:
+        raise ValueError("pick_P: no candidate P fits")
+    if objective == "latency":
+        cost = dict(ok)
+    elif objective == "sm_time":
+        cost = {P: t * min(P, num_sms) for P, t in ok.items()}
+    else:
+        raise ValueError(f"pick_P: unknown objective {objective}")
+    return min(sorted(cost), key=lambda P: cost[P])
+
+
+def plan_batch_P(timings, epochs: int = 1, num_sms: int = 152):
+    """P of every instance of a batch from the autotuner's timings (one {P: epoch ms or None} per
+    instance).  Starts from each instance's least SM-time P; the batch cannot end before
+    bound = epochs x total SM-time / SMs, so an instance whose own epochs take longer than the bound
+    (it would be the critical path) moves to its fastest P, the longest first, each instance once,
+    the bound recomputed after each move."""
+    P = [pick_P(t, "sm_time", num_sms) for t in timings]
+    fast = [pick_P(t, "latency", num_sms) for t in timings]
+    moved = set()
+    while True:
+        bound = epochs * sum(t[p] * min(p, num_sms) for t, p in zip(timings, P)) / num_sms
+        late = [(epochs * timings[x][P[x]], x) for x in range(len(P))
+                if x not in moved and P[x] != fast[x] and epochs * timings[x][P[x]] > bound]
+        if not late:
+            return P
+        x = max(late)[1]
+        P[x] = fast[x]
+        moved.add(x)
+
+
+def autotune_P(cfg: Config, i, j, r, nbr, params: Params, candidates=(4, 8, 16, 32, 64), objective="sm_time",
+               reps=2, stream=None):
+    """Prepares the instance at each candidate P, times one epoch (median of `reps`, CUDA events, on a
+    scratch copy of the parameters) and returns (model prepared at the chosen P, mu, timings)."""
+    timings, best = {}, None
+    num_sms = torch.cuda.get_device_properties(i.device).multi_processor_count
+    for P in candidates:
+        c = Config.make(cfg.M, cfg.N, cfg.F, cfg.K, cfg.L, cfg.bits, cfg.psi_pow, P, list(cfg.alpha), cfg.beta,
+                        list(cfg.lambda_), cfg.rating_scale)
+        m = LshMF(c)
+        try:
+            mu = m.prepare_training(i, j, r, nbr, stream)
+        except LshmfError:
+            timings[P] = None
+            m.close()
+            continue
+        p = params.clone()
+        p.mu = mu
+        ms = []
+        for k in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.train_epoch(p, 0, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if k > 0:
+                ms.append(a.elapsed_time(b))
+        timings[P] = sorted(ms)[len(ms) // 2]
+        if best is None or pick_P({P: timings[P], best[0]: timings[best[0]]}, objective, num_sms) == P:
+            if best is not None:
+                best[1].close()
+            best = (P, m, mu)
+        else:
+            m.close()
+    if best is None:
+        raise ValueError("autotune_P: no candidate P fits")
+    return best[1], best[2], timings
 
 
 def plain_mf_config(cfg: Config) -> Config:

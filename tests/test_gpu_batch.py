@@ -1,0 +1,99 @@
+"""Batched training as one CUDA graph (lshmf_batch_*) vs training each instance alone.
+
+Bar: after the batch (any number of parallel branches) every instance's parameters are
+bit-identical to the same epochs run by separate lshmf_train_epoch calls (those are held to the
+oracle by the parity tests).  Instances are uneven: sizes, densities and P differ.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_2111_11682_gb300 import (GEN_RAND, Batch, LshMF, LshmfError, Params, autotune_P, config_from_workload,
+                                    lshmf)
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(800, 300, 20_000, 4), (2000, 1000, 100_000, 8), (3000, 500, 60_000, 16), (1200, 1500, 40_000, 8),
+          (500, 200, 8_000, 2), (1500, 700, 30_000, 32)]
+
+
+def T(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
+
+
+def _instance(x, M, N, nnz, P):
+    w = replace(synth.TINY, name=f"inst{x}", M=M, N=N, nnz=nnz, P=P, seed=100 + x, beta=0.3)
+    d = synth.generate(w)
+    m = LshMF(config_from_workload(w))
+    ti, tj, tr = T(d["train_i"], torch.int32), T(d["train_j"], torch.int32), T(d["train_r"], torch.uint8)
+    nbr = m.build_neighbours_variant(GEN_RAND, seed=x, device="cuda:0")
+    mu = m.prepare_training(ti, tj, tr, nbr)
+    p = Params.from_init(d["U0"], d["V0"], w.K, "cuda:0")
+    p.mu = mu
+    return w, d, m, p, (ti, tj, tr, nbr)
+
+
+@pytest.fixture(scope="module")
+def instances():
+    out = [_instance(x, *s) for x, s in enumerate(SHAPES)]
+    yield out
+    for _, _, m, _, _ in out:
+        m.close()
+
+
+@pytest.mark.parametrize("branches,with_cost", [(1, False), (3, False), (8, False), (3, True)])
+def test_batch_equals_separate_calls(instances, branches, with_cost):
+    E0, E = 1, 2
+    alone = []
+    for _, _, m, p, _ in instances:
+        q = p.clone()
+        for e in range(E0, E0 + E):
+            m.train_epoch(q, e)
+        alone.append(q)
+    torch.cuda.synchronize()
+    ps = [p.clone() for _, _, _, p, _ in instances]
+    cost = [float(len(d["train_i"])) for _, d, _, _, _ in instances] if with_cost else None
+    b = Batch([m for _, _, m, _, _ in instances], ps, epoch0=E0, epochs=E, branches=branches, cost=cost)
+    assert b.kernels == sum(E * (w.P + 1) for w, _, _, _, _ in instances)
+    for rep in range(2):       # a replay starts from the parameters the previous run left
+        if rep == 1:
+            for q, (_, _, m, _, _) in zip(alone, instances):
+                for e in range(E0, E0 + E):
+                    m.train_epoch(q, e)
+        b.run()
+        b.check()
+        for x, (q, g) in enumerate(zip(alone, ps)):
+            for name in ("U", "V", "b", "bh", "W", "C"):
+                assert torch.equal(getattr(q, name), getattr(g, name)), (branches, rep, x, name)
+    b.close()
+
+
+def test_batch_rejects_bad_lists(instances):
+    ms = [m for _, _, m, _, _ in instances]
+    ps = [p for _, _, _, p, _ in instances]
+    with pytest.raises(LshmfError) as e:
+        Batch([ms[0], ms[0]], [ps[0], ps[0]])
+    assert e.value.status == lshmf.EINVAL
+    with pytest.raises(LshmfError) as e:
+        Batch(ms[:2], ps[:2], epochs=0)
+    assert e.value.status == lshmf.EINVAL
+    fresh = LshMF(config_from_workload(instances[0][0]))       # never prepared
+    with pytest.raises(LshmfError) as e:
+        Batch([ms[1], fresh], ps[1:3])
+    assert e.value.status == lshmf.ESTATE
+    fresh.close()
+
+
+def test_autotune_returns_a_prepared_model(instances):
+    w, d, m, p, (ti, tj, tr, nbr) = instances[1]
+    tuned, mu, timings = autotune_P(m.cfg, ti, tj, tr, nbr, p, candidates=(2, 4, 8, 16, 32), reps=1)
+    assert set(timings) == {2, 4, 8, 16, 32} and any(t is not None for t in timings.values())
+    assert tuned.cfg.P in timings and timings[tuned.cfg.P] is not None
+    assert mu == pytest.approx(p.mu, abs=0)
+    q = p.clone()
+    tuned.train_epoch(q, 0)
+    tuned.check()
+    tuned.close()
