@@ -26,6 +26,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Hardware work queues for concurrent streams and graph branches (read when CUDA initialises; the
+# default 8 caps the batched-training graph at about 8 concurrent instances).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 
 def parse():
@@ -435,6 +438,7 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
     total = float(sum(nnz_all)) * E
     out = {"what": "%d uneven instances x %d epochs: host loop of lshmf_train_epoch vs one CUDA graph "
                    "(lshmf_batch)" % (n_inst, E),
+           "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
            "instances": n_inst, "ratings": int(sum(nnz_all)), "epochs": E,
            "P_histogram": {str(k): int(v) for k, v in zip(*np.unique([m.cfg.P for m in models], return_counts=True))},
            "moved_to_fastest_P": moved, "setup_s": round(setup_s, 1), "modes": {}}

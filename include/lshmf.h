@@ -314,7 +314,8 @@ lshmf_status lshmf_rmse_noalloc(lshmf_handle *h, const lshmf_params *p, const in
  * alone.  The handles and the parameter arrays must outlive the batch, keep
  * their prepared layout, and not be used by other calls while a run is in
  * flight.  n >= 1, epochs >= 1, branches >= 1, costs >= 0, no handle listed
- * twice (EINVAL).  *out is NULL on failure. */
+ * twice (EINVAL).  Branches run concurrently on at most CUDA_DEVICE_MAX_CONNECTIONS
+ * hardware queues (default 8, at most 32; read when CUDA initialises).  *out is NULL on failure. */
 typedef struct lshmf_batch lshmf_batch;
 lshmf_status lshmf_batch_create(lshmf_handle *const *handles, const lshmf_params *params, const double *cost,
                                 int32_t n, int32_t epoch0, int32_t epochs, int32_t branches, lshmf_batch **out);

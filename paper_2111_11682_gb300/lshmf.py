@@ -306,7 +306,9 @@ class LshMF:
 
 class Batch:
     """lshmf_batch_*: epochs [epoch0, epoch0 + epochs) of every (model, params) pair recorded as one
-    CUDA graph, instances over `branches` parallel branches (round-robin, or longest-first by `cost`).  Keeps references to the
+    CUDA graph, instances over `branches` parallel branches (round-robin, or longest-first by `cost`).
+    Branches run concurrently on at most CUDA_DEVICE_MAX_CONNECTIONS hardware queues (default 8,
+    at most 32; the variable is read when CUDA initialises, so set it before the first CUDA call).  Keeps references to the
     models and parameter tensors (they must stay alive and unchanged in shape while the batch lives)."""
 
     def __init__(self, models, params, epoch0=0, epochs=1, branches=1, cost=None):
