@@ -462,6 +462,24 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
     return out
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Max of a per-rank value over all ranks of the process group (the slowest replica sets the
+    job time); the value itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each process `units_per_rank`
+    units, timed by the slowest rank (`ms` per step)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -537,13 +555,9 @@ def run_ours(args, rank, world, local_rank):
     launches = launch_count() - l0
     ms_total = ev0.elapsed_time(ev1)
     epoch_ms = [a.elapsed_time(b) for a, b in epoch_events]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
-    value = world * E * nnz / (ms_step / 1e3)
+    value = replica_throughput(E * nnz, world, ms_step)
 
     e2e = None
     if not args.no_e2e:
@@ -556,13 +570,9 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         ms_e2e = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(ms_e2e, world, dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
-        e2e = {"value": world * E * nnz / (ms_e2e / 1e3), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
+        e2e = {"value": replica_throughput(E * nnz, world, ms_e2e), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
 
     topn = None
