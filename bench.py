@@ -142,6 +142,13 @@ def sgd_bytes_per_epoch(stats, w):
     return nnz * (4 + 1 + w.K / 8 + 8 * w.F + 8) + stats["explicit_neighbours"]
 
 
+def sgd_min_bytes_per_epoch(stats, w):
+    """Compulsory bytes of one epoch: the rating stream (4 + 1 + K/8 B per rating plus the explicit
+    neighbour ratings) and one read and one write of every parameter (U, V, b, bhat, W, C, FP32)."""
+    params = 4 * (w.M * w.F + w.N * w.F + w.M + w.N + 2 * w.N * w.K)
+    return stats["nnz"] * (4 + 1 + w.K / 8) + stats["explicit_neighbours"] + 2 * params
+
+
 def measure_topn(m, p, w, dev, sizes=(1, 64, 1024, 4096), reps=20, n=10, seed=0):
     """Top-N serving (lshmf_topn, Eq. (1) over all items): latency of one call for batches of
     query users of several sizes (users drawn uniformly, inputs resident in HBM), for the FP32
@@ -597,6 +604,9 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": "k_sgd_stratum (one epoch = P launches)", "achieved": round(achieved, 1),
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": traffic, "algorithmic_bytes_per_epoch": int(bytes_ep), "launches_per_epoch": P,
+            "algorithmic_bytes_per_launch": int(bytes_ep / P),
+            "min_bytes_per_epoch": int(sgd_min_bytes_per_epoch(stats, w)),
+            "min_bytes_achieved_gbs": round(sgd_min_bytes_per_epoch(stats, w) / (ep_med / 1e3) / 1e9, 1),
             "epoch_ms_median": round(ep_med, 3), "note": f"frac of {peak_kind} HBM copy bandwidth"}
 
     out = {"metric": "SGD rating-updates/s per epoch at RMSE parity (whole training job)", "value": value,
