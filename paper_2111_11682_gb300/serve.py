@@ -9,9 +9,11 @@ order: consecutive queries are merged into one lshmf_topn call (up to
 an update runs once every query that arrived before it has been answered, and
 every request records its latency from arrival to completion.  Admission:
 a call starts only if free device memory covers its scratch estimate plus a
-reserve; otherwise the request completes with an error message.  A query's answer does
-not depend on the queries it is batched with (both top-N modes score each user
-on its own), only on the updates applied before it.
+reserve; otherwise the request completes with an error message, as does a
+query naming a user outside the model (alone, so the rest of its batch is
+still served) or a call the library rejects.  A query's answer does not depend
+on the queries it is batched with (both top-N modes score each user on its
+own), only on the updates applied before it.
 
 This module is host-side plumbing: it marshals requests into the library's
 calls and owns no arithmetic of the method.
@@ -29,7 +31,7 @@ import torch
 from .lshmf import LshMF, Params
 
 
-@dataclass
+@dataclass(eq=False)          # requests compare by identity
 class Request:
     kind: str                     # "topn" or "ingest"
     payload: tuple
@@ -114,17 +116,33 @@ class Server:
                 self._finish(batch, error="not enough free device memory")
                 return True
             t = lambda a, dt: torch.from_numpy(a).to(dev, dt)
-            self.m.ingest(M_new, N_new, t(i, torch.int32), t(j, torch.int32), t(r, torch.uint8), self.H,
-                          self.nbr[: self.m.cfg.N + N_new], self.p, local_epochs=self.local_epochs)
+            try:
+                self.m.ingest(M_new, N_new, t(i, torch.int32), t(j, torch.int32), t(r, torch.uint8), self.H,
+                              self.nbr[: self.m.cfg.N + N_new], self.p, local_epochs=self.local_epochs)
+            except Exception as e:          # a rejected increment leaves the model as it was
+                self._finish(batch, error=str(e))
+                return True
             self.calls["ingest"] += 1
             self._finish(batch, results=[(self.m.cfg.M, self.m.cfg.N)])
             return True
+        # a query with a user outside the current model fails alone instead of failing its batch
+        M = self.m.cfg.M
+        bad = [q for q in batch if len(q.payload[0]) and (q.payload[0].min() < 0 or q.payload[0].max() >= M)]
+        if bad:
+            self._finish(bad, error=f"user id outside [0, {M})")
+            batch = [q for q in batch if q not in bad]
+            if not batch:
+                return True
         users = np.concatenate([q.payload[0] for q in batch])
         if not self._admit(len(users) * (256 + self.n) * 8):
             self._finish(batch, error="not enough free device memory")
             return True
-        items, scores = self.m.topn(self.p, torch.from_numpy(users).to(dev), self.n, mode=self.mode)
-        items, scores = items.cpu().numpy(), scores.cpu().numpy()   # synchronises
+        try:
+            items, scores = self.m.topn(self.p, torch.from_numpy(users).to(dev), self.n, mode=self.mode)
+            items, scores = items.cpu().numpy(), scores.cpu().numpy()   # synchronises
+        except Exception as e:
+            self._finish(batch, error=str(e))
+            return True
         self.calls["topn"] += 1
         self.users_served += len(users)
         out, k = [], 0

@@ -123,3 +123,24 @@ def test_latency_summary_and_poisson_arrivals():
     s = latency_summary(reqs + [bad])
     assert s["requests"] == 100 and s["failed"] == 1
     assert s["p50_ms"] == pytest.approx(50.5) and s["max_ms"] == pytest.approx(100.0)
+
+
+def test_bad_query_fails_alone_and_errors_do_not_stop_the_loop(plenty):
+    m = FakeModel(M=50)
+    s = _server(m)
+    good = s.submit_topn(np.array([1, 2]))
+    bad = s.submit_topn(np.array([3, 50]))          # user 50 is outside the model
+    good2 = s.submit_topn(np.array([4]))
+    while s.step():
+        pass
+    assert bad.error and "outside" in bad.error and bad.result is None
+    assert good.error is None and good2.error is None and m.calls == [("topn", 3)]
+
+    def boom(*a, **k):
+        raise RuntimeError("EINVAL: rejected")
+    m.ingest = boom
+    u = s.submit_ingest(1, 1, np.array([50]), np.array([40]), np.array([3]))
+    after = s.submit_topn(np.array([5]))
+    while s.step():
+        pass
+    assert "rejected" in u.error and after.error is None and m.cfg.M == 50
