@@ -7,14 +7,15 @@
 // values the sequential order gives it: its item's parameters after the item's
 // previous rating, its user's after the user's previous rating.
 //
-// Execution.  One launch per stratum with one persistent CTA per SM.  A CTA
-// takes the stratum's blocks from a global counter (heaviest first), loads a
-// block's user table into a free block slot and appends the block's item runs
-// ("segments") to a CTA queue.  Warps are organised in groups: one consumer
-// warp and GP producer warps.  A group takes segments from the queue in queue
-// order and cuts them into chunks of at most CH ratings; its chunks form a
-// stream, and producer p of the group prepares stream positions p, p + GP, ...
-// while the consumer runs them in order.  A chunk may be prepared once every
+// Execution.  One launch per stratum with one persistent CTA per SM.  A CTA's
+// scheduler warp takes the stratum's blocks from a global counter (heaviest
+// first), loads a block's user table into a free block slot and hands the
+// block's item runs ("segments"), in order, to the CTA's groups of one
+// consumer warp and GP producer warps (each run to the group with the least
+// work not yet consumed).  A group cuts its runs into chunks of at most CH
+// ratings; its chunks form a stream, and producer p of the group prepares
+// stream positions p, p + GP, ... while the consumer runs them in order.
+// Producers take no lock: they wait for the group's end position.  A chunk may be prepared once every
 // user of the chunk has finished its earlier ratings of the block (per-user
 // counters in the block slot); the consumer then runs the item chain.
 //
@@ -40,10 +41,10 @@
 // e = T (r - base), and replays the n steps of Eq. 5 with those errors: item
 // state, u_i, b_i.
 //
-// Progress.  Segments are taken in queue order, chunks are prepared and run
-// in stream order, and a chunk waits only for ratings of earlier segments of
-// its block.  The oldest unfinished segment of a CTA therefore never waits on
-// a user, and every wait is bounded: after SGD_SPIN_LIMIT polls the kernel
+// Progress.  Segments are handed out in block order, each group's in that
+// order, chunks are prepared and run in stream order, and a chunk waits only
+// for ratings of earlier segments of its block.  The oldest unfinished segment
+// of a CTA therefore never waits on a user, and every wait is bounded: after SGD_SPIN_LIMIT polls the kernel
 // records a timeout, raises the CTA's abort flag and returns.
 #include <cuda/atomic>
 
@@ -60,12 +61,11 @@ constexpr unsigned SGD_SUSPEND_NS = 1000; // suspend-time hint of one try
 constexpr int CH = SGD_CH;    // ratings per chunk (the chunk layout of prepare_training uses the same size)
 constexpr int GP = 3;         // producer warps per group
 constexpr int NRING = 4;      // chunk buffers per group
-constexpr int GRAB = 1;       // segments a group takes from the CTA queue at once (at most)
 constexpr int GQN = 32;       // group segment list (ring)
 constexpr int MAX_GROUPS = 4;
 constexpr int MAX_SLOTS = 4;  // blocks in flight per CTA
 
-static_assert(NRING > 1 && GQN >= NRING + GP + GRAB + 2, "group segment ring too small");
+static_assert(NRING > 1 && GQN >= NRING + GP + 2, "group segment ring too small");
 
 // Decay tables: row g of pow holds q_g^m, of inv q_g^-m (m = 0..CH), g = bh, v, w, c.
 enum { QT_BH = 0, QT_V = 1, QT_W = 2, QT_C = 3 };
@@ -90,7 +90,7 @@ struct SgdArgs {
   float mu, inv_scale;
   float gam[6], lam[6];
   float qpow[4][CH + 1], qinv[4][CH + 1];
-  int F, K, P, mw, maxu, cqn, nslots;
+  int F, K, P, mw, maxu, nslots;
   int want_sq;      // accumulate sum of e^2 per segment
   int32_t *err;
 };
@@ -164,8 +164,7 @@ struct __align__(16) Scratch {
   float L[CH][CH];
 };
 
-// A segment (one item's run of ratings inside a block) as the CTA queue and
-// the groups hold it.
+// A segment (one item's run of ratings inside a block) as a group holds it.
 struct SegInfo {
   int seg;      // segment id
   int slot;     // block slot of its block
@@ -183,18 +182,17 @@ struct __align__(16) Group {
   Scratch<KPL> scr[GP];
   uint64_t full[NRING];  // phase k completes when position k * NRING + x is in ring[x] (32 arrivals)
   uint64_t empty[NRING]; // phase k completes when the consumer is done with position k * NRING + x
-  SegInfo ent[GQN];      // the group's e-th segment (ring)
+  SegInfo ent[GQN];      // the group's e-th segment (ring; written by the scheduler warp only)
   int start[GQN];        // stream position of its first chunk
-  int ngrab;             // segments taken
-  int endpos;            // stream position after the last segment taken
-  int done;              // no more segments
-  int lock;
+  int endpos;            // stream position after the last segment handed to the group
+  int done;              // no more segments (released after the last endpos)
+  int pcur[GP];          // per producer: oldest segment index it may still read
+  int cpos;              // positions the consumer has finished
 };
 
 struct CtaCtl {
-  int cq_head, cq_tail, cq_lock, cq_done;
   int abort_;
-  int pad[3];
+  int pad[7];
   int slot_left[MAX_SLOTS];   // segments of the slot's block not finished (0 = slot free)
   int slot_pad[MAX_SLOTS];
 };
@@ -202,7 +200,6 @@ struct CtaCtl {
 struct Smem {
   CtaCtl *ctl;
   float (*qt)[CH + 1];
-  SegInfo *cq;      // [cqn] CTA queue (ring)
   int *users;       // [nslots][maxu]
   int *cnt;         // [nslots][maxu]
 };
@@ -271,15 +268,22 @@ __device__ __forceinline__ void unlock_warp(int *l) {
   if ((threadIdx.x & 31) == 0) st_rel(l, 0);
 }
 
-// ------------------------------------------------------- CTA block queue ----
+// ------------------------------------------------------------ scheduler ----
 // The scheduler warp of a CTA takes the stratum's blocks from a global counter
-// (heaviest first).  For each block it waits for a free block slot and room in
-// the queue, loads the block's user table into the slot and appends the
-// block's segments, with their item, rating range and chunks, to the queue.
-__device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, int s) {
+// (heaviest first).  For each block it waits for a free block slot, loads the
+// block's user table into the slot and hands the block's segments, in order,
+// to the groups: each segment goes to the group with the fewest chunks not yet
+// consumed among those whose segment ring has room (a ring entry is reused
+// only when every producer of the group has moved past it).  Producers take no
+// lock: they wait for their group's end position to pass theirs.
+template <int FPL, int KPL>
+__device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> *grp, int ng, int s) {
   const int lane = threadIdx.x & 31;
   CtaCtl *ctl = sm.ctl;
-  while (true) {
+  int endp[MAX_GROUPS], nseg[MAX_GROUPS];
+  for (int g = 0; g < MAX_GROUPS; ++g) endp[g] = nseg[g] = 0;
+  bool ok = true;
+  while (ok) {
     int bi = 0;
     if (lane == 0) bi = atomicAdd(&a.next_blk[s], 1);
     bi = __shfl_sync(0xffffffffu, bi, 0);
@@ -291,18 +295,16 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, int s) 
     const int64_t u0 = a.blk_user[blk];
     const int nu = int(a.blk_user[blk + 1] - u0);
     const int ns = sg1 - sg0;
-    // a free slot (released by the consumer of its block's last segment) and queue room
+    // a free slot (released by the consumer of its block's last segment)
     int slot = -1, it = 0;
-    const int tail = ctl->cq_tail;
     while (true) {
       if (lane == 0) {
         slot = -1;
-        if (tail + ns - ld_acq(&ctl->cq_head) <= a.cqn)
-          for (int x = 0; x < a.nslots; ++x)
-            if (ld_acq(&ctl->slot_left[x]) == 0) {
-              slot = x;
-              break;
-            }
+        for (int x = 0; x < a.nslots; ++x)
+          if (ld_acq(&ctl->slot_left[x]) == 0) {
+            slot = x;
+            break;
+          }
       }
       slot = __shfl_sync(0xffffffffu, slot, 0);
       if (slot >= 0) break;
@@ -317,60 +319,77 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, int s) 
       us[x] = a.users[u0 + x];
       cn[x] = 0;
     }
-    for (int x = lane; x < ns; x += 32) {
-      const int sg = sg0 + x;
+    __syncwarp();
+    if (lane == 0) ctl->slot_left[slot] = ns;
+    __threadfence_block();   // the user table and the slot count precede every segment of the block
+    __syncwarp();
+    for (int x0 = 0; x0 < ns && ok; x0 += 32) {
+      // lanes load up to 32 segment descriptors, lane 0 hands them out in order
       SegInfo e;
-      e.seg = sg;
-      e.slot = slot;
-      e.j = a.seg_j[sg];
-      const int64_t p0 = a.seg_p0[sg];
-      e.p0 = int(p0);
-      e.n = int(a.seg_p0[sg + 1] - p0);
-      e.ck0 = a.seg_ck[sg];
-      e.nck = a.seg_ck[sg + 1] - e.ck0;
-      e.pad = 0;
-      sm.cq[(tail + x) % a.cqn] = e;
+      if (x0 + lane < ns) {
+        const int sg = sg0 + x0 + lane;
+        e.seg = sg;
+        e.slot = slot;
+        e.j = a.seg_j[sg];
+        const int64_t p0 = a.seg_p0[sg];
+        e.p0 = int(p0);
+        e.n = int(a.seg_p0[sg + 1] - p0);
+        e.ck0 = a.seg_ck[sg];
+        e.nck = a.seg_ck[sg + 1] - e.ck0;
+        e.pad = 0;
+      }
+      const int cnt = min(32, ns - x0);
+      for (int x = 0; x < cnt && ok; ++x) {
+        SegInfo f;
+        f.seg = __shfl_sync(0xffffffffu, e.seg, x);
+        f.slot = slot;
+        f.j = __shfl_sync(0xffffffffu, e.j, x);
+        f.p0 = __shfl_sync(0xffffffffu, e.p0, x);
+        f.n = __shfl_sync(0xffffffffu, e.n, x);
+        f.ck0 = __shfl_sync(0xffffffffu, e.ck0, x);
+        f.nck = __shfl_sync(0xffffffffu, e.nck, x);
+        f.pad = 0;
+        if (lane == 0) {
+          int g = -1, wait = 0;
+          while (true) {
+            int best = 0x7fffffff;
+            for (int h = 0; h < ng; ++h) {
+              int mp = 0x7fffffff;
+              for (int pp = 0; pp < GP; ++pp) mp = min(mp, ld_acq(&grp[h].pcur[pp]));
+              if (nseg[h] >= mp + GQN) continue;                  // ring full
+              const int load = endp[h] - ld_acq(&grp[h].cpos);
+              if (load < best) {
+                best = load;
+                g = h;
+              }
+            }
+            if (g >= 0) break;
+            if (++wait > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+              ok = false;
+              break;
+            }
+            backoff(wait);
+          }
+          if (ok) {
+            Group<FPL, KPL> &G = grp[g];
+            G.ent[nseg[g] % GQN] = f;
+            G.start[nseg[g] % GQN] = endp[g];
+            ++nseg[g];
+            endp[g] += f.nck;
+            __threadfence_block();
+            st_rel(&G.endpos, endp[g]);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
     }
-    __syncwarp();
-    if (lane == 0) {
-      ctl->slot_left[slot] = ns;
-      __threadfence_block();
-      st_rel(&ctl->cq_tail, tail + ns);
-    }
-    __syncwarp();
   }
-  if (lane == 0) st_rel(&ctl->cq_done, 1);
-}
-
-// Takes up to maxn of the next CTA queue entries for a group and copies them
-// to dst[(base + x) % GQN] under the queue lock (before the scheduler can reuse
-// them).  Returns how many (waiting for at least one), 0 when this CTA has no
-// more blocks in the stratum, or -2 on abort.
-__device__ __noinline__ int take_entries(const SgdArgs &a, const Smem &sm, SegInfo *dst, int base, int maxn) {
-  CtaCtl *ctl = sm.ctl;
-  const int lane = threadIdx.x & 31;
-  if (!lock_warp(a, &ctl->cq_lock, ctl)) return -2;
-  int got = 0, it = 0;
-  const int h = ctl->cq_head;
-  while (true) {
-    const int done = ld_acq(&ctl->cq_done);   // read before the tail: a done scheduler has appended everything
-    const int t = ld_acq(&ctl->cq_tail);
-    if (h < t) {
-      got = min(maxn, t - h);
-      if (lane < got) dst[(base + lane) % GQN] = sm.cq[(h + lane) % a.cqn];
-      __syncwarp();
-      if (lane == 0) st_rel(&ctl->cq_head, h + got);
-      break;
-    }
-    if (done) break;
-    if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
-      sgd_abort(a, ctl);
-      return -2;
-    }
-    backoff(it);
+  if (!ok) {
+    sgd_abort(a, ctl);
+    return;
   }
-  unlock_warp(&ctl->cq_lock);
-  return got;
+  if (lane == 0)
+    for (int h = 0; h < ng; ++h) st_rel(&grp[h].done, 1);
 }
 
 // ------------------------------------------------------------- producer ----
@@ -385,56 +404,22 @@ struct Producer {
   __device__ Producer(const SgdArgs &a_, const Smem &sm_, Group<FPL, KPL> &G_, int s_, int p_)
       : a(a_), sm(sm_), G(G_), s(s_), p(p_) {}
 
-  // Makes sure stream position pos is covered by a taken segment.  Returns
-  // 1 when it is, 0 when the group's stream ends before pos, -1 on abort.
-  // The group lock is only tried: while another producer holds it (possibly
-  // waiting for the CTA queue), this producer keeps
-  // re-reading endpos, so a position that is already covered is never held
-  // up behind the lock.
+  // Waits until stream position pos is covered by a segment handed to the
+  // group.  Returns 1 when it is, 0 when the group's stream ends before pos,
+  // -1 on abort.  done is read before endpos: the scheduler releases done after
+  // its last endpos, so a producer that sees done also sees the final end.
   __device__ int cover(int pos) {
     CtaCtl *ctl = sm.ctl;
     int it = 0;
     while (true) {
-      const int endp = ld_acq(&G.endpos);
-      if (pos < endp) return 1;
-      if (ld_acq(&G.done)) return 0;
-      int got = 0;
-      if ((threadIdx.x & 31) == 0) got = atomicCAS(&G.lock, 0, 1) == 0;
-      got = __shfl_sync(0xffffffffu, got, 0);
-      if (!got) {
-        if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
-          sgd_abort(a, ctl);
-          return -1;
-        }
-        backoff(it);
-        continue;
+      const int d = ld_acq(&G.done);
+      if (pos < ld_acq(&G.endpos)) return 1;
+      if (d) return 0;
+      if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+        sgd_abort(a, ctl);
+        return -1;
       }
-      __threadfence_block();
-      if (pos >= G.endpos && !G.done) {
-        const int g = G.ngrab;
-        const int got = take_entries(a, sm, G.ent, g, GRAB);
-        if (got == -2) {
-          unlock_warp(&G.lock);
-          return -1;
-        }
-        const int lane = threadIdx.x & 31;
-        __syncwarp();
-        if (lane == 0) {
-          if (got == 0) {
-            st_rel(&G.done, 1);
-          } else {
-            int st = G.endpos;
-            for (int x = 0; x < got; ++x) {
-              G.start[(g + x) % GQN] = st;
-              st += G.ent[(g + x) % GQN].nck;
-            }
-            G.ngrab = g + got;
-            __threadfence_block();
-            st_rel(&G.endpos, st);
-          }
-        }
-      }
-      unlock_warp(&G.lock);
+      backoff(it);
     }
   }
 
@@ -460,6 +445,8 @@ struct Producer {
     while (!(pos < G.start[cur % GQN] + G.ent[cur % GQN].nck)) ++cur;
     const SegInfo E = G.ent[cur % GQN];
     const int k = pos - G.start[cur % GQN];
+    __syncwarp();
+    if (lane == 0) st_rel(&G.pcur[p], cur);   // entries before cur are never read again by this producer
     const int nk = E.nck, sg = E.seg, slot = E.slot;
     // chunk metadata (one rating per lane) and neighbour baselines
     const int32_t j = E.j;
@@ -836,6 +823,7 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
       atomicSub(&ctl->slot_left[slot], 1);
     }
     mbar_arrive(&G.empty[buf]);   // every lane's reads of the chunk are done
+    if (lane == 0) st_rel(&G.cpos, pos + 1);
   }
 }
 
@@ -844,7 +832,7 @@ __global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
 k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
-  // carve shared memory: [groups][ctl][qt][queue][users][cnt]
+  // carve shared memory: [groups][ctl][qt][users][cnt]
   Group<FPL, KPL> *grp = reinterpret_cast<Group<FPL, KPL> *>(smem_raw);
   unsigned char *ptr = smem_raw + sizeof(Group<FPL, KPL>) * ngroups;
   Smem sm;
@@ -852,8 +840,6 @@ k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   ptr += sizeof(CtaCtl);
   sm.qt = reinterpret_cast<float(*)[CH + 1]>(ptr);
   ptr += sizeof(float) * 8 * (CH + 1);
-  sm.cq = reinterpret_cast<SegInfo *>(ptr);
-  ptr += sizeof(SegInfo) * a.cqn;
   sm.users = reinterpret_cast<int *>(ptr);
   ptr += sizeof(int) * a.nslots * a.maxu;
   sm.cnt = reinterpret_cast<int *>(ptr);
@@ -875,7 +861,7 @@ k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   // warps 0..ngroups-1 are the consumers (one per warp scheduler), then the
   // producers, then the block scheduler
   if (wid == ngroups * (GP + 1)) {
-    scheduler(a, sm, s);
+    scheduler<FPL, KPL>(a, sm, grp, ngroups, s);
   } else if (wid < ngroups) {
     consumer<FPL, KPL>(a, sm, grp[wid]);
   } else if (wid < ngroups * (GP + 1)) {
@@ -905,21 +891,17 @@ __global__ void k_sum_seg_sq(const double *x, int64_t n, double *out) {
 
 template <int FPL, int KPL>
 static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
-  // groups and block slots: as many as fit (the queue holds the segments of every slot's block)
+  // groups and block slots: as many as fit
   const size_t gsz = sizeof(Group<FPL, KPL>);
-  const int maxseg = a.cqn;
   auto need = [&](int ng, int ns) {
-    return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + sizeof(SegInfo) * size_t(ns) * maxseg +
-           2 * sizeof(int) * size_t(ns) * a.maxu;
+    return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + 2 * sizeof(int) * size_t(ns) * a.maxu;
   };
   int ng = MAX_GROUPS, ns = MAX_SLOTS;
   while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
   while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
   if (need(ng, ns) > size_t(h->smem_optin))
-    return set_err(h, LSHMF_EINVAL, "train: %d users or %d segments in one block exceed shared memory; raise P",
-                   a.maxu, maxseg);
+    return set_err(h, LSHMF_EINVAL, "train: %d users in one block exceed shared memory; raise P", a.maxu);
   a.nslots = ns;
-  a.cqn = ns * maxseg;
   const size_t smem = need(ng, ns);
   // the attribute is a per-kernel cap shared by every handle: set it to the device maximum so that
   // launches of handles with different block sizes (captured together into one graph, or issued from
@@ -984,7 +966,6 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
     }
   }
   a.F = c.F; a.K = c.K; a.P = c.P; a.mw = tl.mask_words; a.maxu = std::max(1, tl.max_users_per_block);
-  a.cqn = std::max(1, tl.max_segs_per_block);   // segments per block; the queue size is set at launch
   a.nslots = 1;
   a.want_sq = h_sq != nullptr;
   a.err = h->d_err;
