@@ -469,6 +469,15 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
     return out
 
 
+def epoch_split(epoch_ms, E):
+    """Median time of each job's first epoch and of its later epochs (epoch_ms holds E epochs per
+    job, jobs back to back); the later ones are None for a one-epoch job."""
+    x = np.asarray(epoch_ms, dtype=np.float64).reshape(-1, E)
+    first = float(np.median(x[:, 0]))
+    rest = float(np.median(x[:, 1:])) if E > 1 else None
+    return first, rest
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """Max of a per-rank value over all ranks of the process group (the slowest replica sets the
     job time); the value itself on one rank."""
@@ -618,7 +627,9 @@ def run_ours(args, rank, world, local_rank):
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-           "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3), "layout": stats,
+           "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3),
+           "epoch_ms_first_and_later": [None if v is None else round(v, 3) for v in epoch_split(epoch_ms, E)],
+           "layout": stats,
            "topn": topn, "ingest": ingest, "serving": serving, "generators": generators, "batch": batch,
            "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:

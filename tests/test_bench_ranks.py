@@ -43,3 +43,11 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
     assert bench.replica_throughput(10.0, 1, 1000.0) == 10.0
+
+
+def test_epoch_split_first_and_later():
+    import bench
+    ms = [10.0, 5.0, 6.0, 12.0, 5.5, 6.5]        # two jobs of three epochs
+    first, rest = bench.epoch_split(ms, 3)
+    assert first == 11.0 and rest == 5.75
+    assert bench.epoch_split([3.0, 4.0], 1) == (3.5, None)
