@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -74,10 +74,29 @@ def _load():
         fn.restype = ctypes.c_int
     lib.oracle_rating_step.restype = ctypes.c_double
     lib.oracle_mean.restype = ctypes.c_double
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_threads.restype = ctypes.c_int
     lib.oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
     lib.oracle_splitmix64.restype = ctypes.c_uint64
     _lib = lib
     return lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the item loop of Eq. (3) and the block loop of a stratum (1 = serial).
+    Results are bit-identical for every thread count.  Returns the previous setting."""
+    global _threads
+    prev = _threads
+    _threads = max(1, int(n))
+    _load().oracle_set_threads(_threads)
+    return prev
+
+
+def get_threads() -> int:
+    return _threads
+
+
+_threads = 1
 
 
 def _p(a):

@@ -52,6 +52,18 @@
 #define ORC_EINVAL -1
 #define ORC_ENOMEM -2
 
+/* Host threads for the two loops whose iterations are independent by
+ * definition: the items of Eq. (3) and the P blocks of one stratum (they share
+ * no user and no item, and term (2) reads the epoch-start bhat snapshot).
+ * Every thread count gives bit-identical results: each iteration's arithmetic
+ * is the same sequential code, and per-block sums are combined in block order. */
+static int g_threads = 1;
+
+int oracle_set_threads(int n) {
+  g_threads = n < 1 ? 1 : n;
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 4.1, Eq. (3): simLSH pre-sign sums and signatures               */
 /* ------------------------------------------------------------------ */
@@ -72,13 +84,15 @@ int oracle_signature_sums(int64_t M, int64_t N, int32_t L, int32_t bits, int32_t
                           const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
                           const uint64_t *H, int32_t W, int64_t *sums) {
   if (L <= 0 || bits <= 0 || bits > 32 || (int64_t)L * bits > 64LL * W) return ORC_EINVAL;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads) reduction(| : bad)
   for (int64_t j = 0; j < N; ++j) {
     for (int32_t t = 0; t < L; ++t) {
       for (int32_t g = 0; g < bits; ++g) {
         int64_t s = 0;
         for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) {
           int64_t i = row[p];
-          if (i < 0 || i >= M) return ORC_EINVAL;
+          if (i < 0 || i >= M) { bad = 1; break; }
           int64_t phi = hbit(H, W, i, (int64_t)t * bits + g) ? 1 : -1;
           s += psi(r[p], psi_pow) * phi;
         }
@@ -86,7 +100,7 @@ int oracle_signature_sums(int64_t M, int64_t N, int32_t L, int32_t bits, int32_t
       }
     }
   }
-  return ORC_OK;
+  return bad ? ORC_EINVAL : ORC_OK;
 }
 
 /* sig[t * N + j] = Upsilon applied bitwise: bit g set iff the sum is >= 0. */
@@ -452,22 +466,35 @@ int oracle_train(const oracle_cfg *c, int64_t nnz, const int32_t *ti, const int3
   double tfac = 1.0 + c->beta * pow((double)epoch, 1.5);   /* Eq. (7) */
   for (int g = 0; g < 6; ++g) { gam[g] = c->alpha[g] / tfac; lam[g] = c->lambda[g]; }
 
-  uint8_t expl[1024];
-  double rnb[1024], bnb[1024];
+  /* The blocks of a stratum share no user and no item, so they may run in any
+   * order or at once; each block's sum of e^2 is kept and the stratum's sums
+   * are added in block order (the same total for every thread count). */
   double se = 0.0;
+  double *blk_se = (double *)malloc(sizeof(double) * (size_t)P);
+  if (!blk_se) {
+    free(bptr); free(bfill); free(rat); free(bh0); free_user_lists(&ul);
+    return ORC_ENOMEM;
+  }
   for (int64_t s = s_begin; s < s_end; ++s) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
     for (int64_t q = 0; q < P; ++q) {
+      uint8_t expl[1024];
+      double rnb[1024], bnb[1024];
       int64_t rb = (q + s) % P, cb = q;
       int64_t blk = cb * P + rb;
+      double bse = 0.0;
       for (int64_t p = bptr[blk]; p < bptr[blk + 1]; ++p) {
         int64_t i = rat[p].i, j = rat[p].j;
         neighbours_of(c, &ul, i, j, nbr, bh0, expl, rnb, bnb);
         double e = oracle_rating_step(F, K, (double)rat[p].r / c->rating_scale, mu, U + i * F, V + j * F,
                                       b + i, bh + j, W + j * K, C + j * K, expl, rnb, bnb, gam, lam);
-        se += e * e;
+        bse += e * e;
       }
+      blk_se[q] = bse;
     }
+    for (int64_t q = 0; q < P; ++q) se += blk_se[q];
   }
+  free(blk_se);
   if (sq_err) *sq_err = se;
   free(bptr); free(bfill); free(rat); free(bh0); free_user_lists(&ul);
   return ORC_OK;
