@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the top-N and online-update measurements")
+    ap.add_argument("--no-large", action="store_true", help="skip the full-size Yahoo!-shaped workload")
     ap.add_argument("--epochs", type=int, default=0, help="epochs per job (0 = the workload's; other values are for profiling only)")
     return ap.parse_args()
 
@@ -111,23 +112,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_from_profile(src_hash):
-    """Per-launch DRAM bytes of the SGD kernel from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "sgd_stratum_traffic.json")
+def profile_entry(kernel, workload, src_hash):
+    """Per-launch DRAM bytes of a kernel on a workload from the committed ncu summary
+    (profiles/dram_traffic.json), if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_source_sha1") == src_hash:
-            return d
+        e = d.get(kernel, {}).get(workload)
+        if e and e.get("kernel_source_sha1") == src_hash:
+            return e
     except Exception:
         pass
     return None
 
 
-def kernel_hash():
+def kernel_hash(files=("sgd.cu", "common.cuh")):
     h = hashlib.sha1()
-    for fn in ("sgd.cu", "common.cuh"):
+    for fn in files:
         with open(os.path.join(ROOT, "paper_2111_11682_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -147,6 +149,96 @@ def sgd_min_bytes_per_epoch(stats, w):
     neighbour ratings) and one read and one write of every parameter (U, V, b, bhat, W, C, FP32)."""
     params = 4 * (w.M * w.F + w.N * w.F + w.M + w.N + 2 * w.N * w.K)
     return stats["nnz"] * (4 + 1 + w.K / 8) + stats["explicit_neighbours"] + 2 * params
+
+
+def sig_bytes(w, nnz):
+    """Algorithmic bytes of the signature stage (Sec. 4.1, Eq. 3) for one call: the CSC read once
+    (4 B row + 1 B rating per rating, 8 B column pointer per item), the users' hash words read once
+    (8 W B per user, W = ceil(L bits / 64)), the keys written (4 L B per item) and the kept pre-sign
+    sums written (8 B per padded hash bit per item: 64 Wp bits, Wp = W rounded up to 1-4, 8 or 16)."""
+    Wh = (w.L * w.bits + 63) // 64
+    Wp = Wh if Wh <= 4 else (8 if Wh <= 8 else 16)
+    return 5 * nnz + 8 * (w.N + 1) + 8 * Wh * w.M + 4 * w.L * w.N + 8 * 64 * Wp * w.N
+
+
+def measure_signatures(m, col_ptr, row, rc, H, w, reps=10):
+    """lshmf_signatures (the Eq. (3) stage alone) on the workload's CSC: CUDA events around one call
+    on the current stream, median of `reps` after two warm-ups; roofline of its algorithmic bytes."""
+    import torch
+
+    sig = torch.empty((w.L, w.N), dtype=torch.int32, device=row.device)
+    ms = []
+    stream = torch.cuda.current_stream()
+    for k in range(reps + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.signatures(col_ptr, row, rc, H, sig_out=sig)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            ms.append(a.elapsed_time(b))
+    m.check()
+    med = float(np.median(ms))
+    nnz = int(row.numel())
+    byts = sig_bytes(w, nnz)
+    peak, peak_kind = peaks()
+    ach = byts / (med / 1e3) / 1e9
+    prof = profile_entry("signatures", w.name, kernel_hash(("simlsh.cu", "common.cuh")))
+    return {"what": "lshmf_signatures: simLSH keys of all items (Eq. 3) and the kept pre-sign sums",
+            "ms_median": round(med, 4), "ms_all": [round(x, 4) for x in ms],
+            "ratings_per_s": nnz / (med / 1e3),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+                         "algorithmic_bytes": int(byts), "note": f"frac of {peak_kind} HBM copy bandwidth",
+                         "int_adds_per_rating_naive": w.L * w.bits}}
+
+
+def gpu_job_rmse(ws, d, dev, P=None):
+    """The whole job on the GPU through the library (COO -> CSC, neighbour build, layout, every epoch)
+    on workload `ws` and its held-out RMSE (Eq. 6)."""
+    import torch
+
+    from paper_2111_11682_gb300 import LshMF, Params, config_from_workload
+
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    m = LshMF(config_from_workload(ws, P))
+    ti, tj, tr = t(d["train_i"], torch.int32), t(d["train_j"], torch.int32), t(d["train_r"], torch.uint8)
+    col_ptr, row, rc = m.csc_from_coo(ti, tj, tr)
+    nbr = m.build_neighbours(col_ptr, row, rc, t(d["H"].view(np.int64), torch.int64))
+    p = Params.from_init(d["U0"], d["V0"], ws.K, dev)
+    p.mu = m.prepare_training(ti, tj, tr, nbr)
+    for e in range(ws.epochs):
+        m.train_epoch(p, e)
+    rm = m.rmse(p, t(d["test_i"], torch.int32), t(d["test_j"], torch.int32), t(d["test_r"], torch.uint8))
+    m.close()
+    return rm
+
+
+def rmse_parity(gpu, orc, sample, bar=2e-3):
+    rel = abs(gpu - orc) / orc
+    return {"gpu": gpu, "oracle": orc, "rel": rel, "bar": bar, "pass": bool(rel <= bar), "sample": sample}
+
+
+def host_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def measure_topn(m, p, w, dev, sizes=(1, 64, 1024, 4096), reps=20, n=10, seed=0):
@@ -496,11 +588,132 @@ def replica_throughput(units_per_rank: float, world: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
+def sgd_roofline(stats, w, epoch_ms, P):
+    peak, peak_kind = peaks()
+    ep_med = float(np.median(epoch_ms))
+    bytes_ep = sgd_bytes_per_epoch(stats, w)
+    achieved = bytes_ep / (ep_med / 1e3) / 1e9
+    prof = profile_entry("sgd_epoch", w.name, kernel_hash())
+    return {"bound": "hbm", "kernel": "SGD epoch kernel", "achieved": round(achieved, 1),
+            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+            "algorithmic_bytes_per_epoch": int(bytes_ep),
+            "min_bytes_per_epoch": int(sgd_min_bytes_per_epoch(stats, w)),
+            "min_bytes_achieved_gbs": round(sgd_min_bytes_per_epoch(stats, w) / (ep_med / 1e3) / 1e9, 1),
+            "epoch_ms_median": round(ep_med, 3), "P": P, "note": f"frac of {peak_kind} HBM copy bandwidth"}
+
+
+class Job:
+    """One whole training job through the library on device-resident inputs: COO -> CSC, simLSH
+    neighbour build, training layout, every epoch, held-out RMSE."""
+
+    def __init__(self, w, P, dv, dev, epochs):
+        from paper_2111_11682_gb300 import LshMF, Params, config_from_workload
+
+        self.w, self.P, self.dv, self.E = w, P, dv, epochs
+        self.m = LshMF(config_from_workload(w, P))
+        self.init = Params.from_init(dv["U0"], dv["V0"], w.K, dev)
+        self.p = self.init.clone()
+        self.epoch_events = []
+
+    def run(self, src, record_epochs, stream):
+        import torch
+
+        m, p = self.m, self.p
+        if src is self.dv:
+            p.copy_(self.init)
+        col_ptr, row, rc = m.csc_from_coo(src["train_i"], src["train_j"], src["train_r"])
+        nbr = m.build_neighbours(col_ptr, row, rc, src["H"])
+        p.mu = m.prepare_training(src["train_i"], src["train_j"], src["train_r"], nbr)
+        for e in range(self.E):
+            if record_epochs:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                m.train_epoch(p, e)
+                b.record(stream)
+                self.epoch_events.append((a, b))
+            else:
+                m.train_epoch(p, e)
+        return m.rmse(p, src["test_i"], src["test_j"], src["test_r"])
+
+
+def upload(d, dev, pin=True):
+    import torch
+
+    host = {k: torch.from_numpy(np.ascontiguousarray(d[k])) for k in
+            ("train_i", "train_j", "train_r", "test_i", "test_j", "test_r", "U0", "V0")}
+    host["H"] = torch.from_numpy(np.ascontiguousarray(d["H"]).view(np.int64))
+    if pin:
+        host = {k: v.pin_memory() for k, v in host.items()}
+    return host, {k: v.to(dev) for k, v in host.items()}
+
+
+def measure_large(dev, steps=2, warmup=1):
+    """The Yahoo!-shaped large workload at full size on one GPU (1M users x 625k items, 250M ratings
+    0..100, F = 128, K = 32, 32 tables x 16 bits, Psi = r^4 with int64 sums, 5 epochs): whole jobs
+    timed with CUDA events (inputs resident in HBM), the signature stage alone, both rooflines, and
+    the GPU-vs-oracle RMSE gate on a reduced sample of the same shape (4,000 users x 10,000 items,
+    1M ratings, P = 64; the full item count would make the oracle's top-K all-pairs)."""
+    import dataclasses
+
+    import torch
+
+    import oracle
+    import synth
+
+    w = synth.LARGE
+    t0 = time.time()
+    d = synth.generate(w)
+    gen_s = time.time() - t0
+    nnz = len(d["train_i"])
+    host, dv = upload(d, dev, pin=False)
+    del host
+    stream = torch.cuda.current_stream()
+    job = Job(w, w.P, dv, dev, w.epochs)
+    jobs_ms = []
+    for k in range(warmup + steps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rm = job.run(dv, k >= warmup, stream)
+        b.record(stream)
+        b.synchronize()
+        if k >= warmup:
+            jobs_ms.append(a.elapsed_time(b))
+    stats = job.m.training_stats()
+    epoch_ms = [a.elapsed_time(b) for a, b in job.epoch_events]
+    col_ptr, row, rc = job.m.csc_from_coo(dv["train_i"], dv["train_j"], dv["train_r"])
+    sig = measure_signatures(job.m, col_ptr, row, rc, dv["H"], w)
+    job.m.close()
+    del col_ptr, row, rc, dv, job
+    torch.cuda.empty_cache()
+    ms = float(np.median(jobs_ms))
+    # RMSE gate on a reduced sample of the same shape: oracle on every host core, GPU through the library
+    ws = dataclasses.replace(synth.scaled(w, 0.004), N=10_000, nnz=1_000_000, P=64,
+                             name="large-shape 4kx10k-1M")
+    ds = synth.generate(ws)
+    prev = oracle.set_threads(os.cpu_count() or 1)
+    try:
+        rm_o = oracle_job(ws, ds)["rmse_heldout"]
+    finally:
+        oracle.set_threads(prev)
+    rm_g = gpu_job_rmse(ws, ds, dev)
+    return {"workload": w.name, "M": w.M, "N": w.N, "nnz_train": nnz, "F": w.F, "K": w.K, "L": w.L,
+            "bits": w.bits, "psi_pow": w.psi_pow, "epochs": w.epochs, "P": w.P,
+            "value": w.epochs * nnz / (ms / 1e3), "unit": "rating-updates/s", "ms_per_job": round(ms, 2),
+            "jobs_ms": [round(x, 2) for x in jobs_ms], "rmse_heldout": rm,
+            "epoch_rating_updates_per_s": nnz / (float(np.median(epoch_ms)) / 1e3),
+            "epoch_ms_first_and_later": [None if v is None else round(v, 3) for v in epoch_split(epoch_ms, w.epochs)],
+            "roofline": {"sgd": sgd_roofline(stats, w, epoch_ms, w.P), "signatures": sig["roofline"]},
+            "signatures": {k: v for k, v in sig.items() if k != "roofline"},
+            "rmse_parity": rmse_parity(rm_g, rm_o, ws.name), "layout": stats, "generate_s": round(gen_s, 1)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import synth
-    from paper_2111_11682_gb300 import LshMF, Params, config_from_workload, launch_count
+    from paper_2111_11682_gb300 import launch_count
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -514,31 +727,10 @@ def run_ours(args, rank, world, local_rank):
     gen_s = time.time() - t0
     E = args.epochs or w.epochs
     nnz = len(d["train_i"])
-    host = {k: torch.from_numpy(np.ascontiguousarray(d[k])).pin_memory()
-            for k in ("train_i", "train_j", "train_r", "test_i", "test_j", "test_r", "U0", "V0")}
-    host["H"] = torch.from_numpy(np.ascontiguousarray(d["H"]).view(np.int64)).pin_memory()
-    dv = {k: v.to(dev) for k, v in host.items()}
-    m = LshMF(config_from_workload(w, P))
-    init = Params.from_init(dv["U0"], dv["V0"], w.K, dev)
-    p = init.clone()
+    host, dv = upload(d, dev)
     stream = torch.cuda.current_stream()
-    epoch_events = []
-
-    def job(src, record_epochs):
-        p.copy_(init) if src is dv else None
-        col_ptr, row, rc = m.csc_from_coo(src["train_i"], src["train_j"], src["train_r"])
-        nbr = m.build_neighbours(col_ptr, row, rc, src["H"])
-        p.mu = m.prepare_training(src["train_i"], src["train_j"], src["train_r"], nbr)
-        for e in range(E):
-            if record_epochs:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                m.train_epoch(p, e)
-                b.record(stream)
-                epoch_events.append((a, b))
-            else:
-                m.train_epoch(p, e)
-        return m.rmse(p, src["test_i"], src["test_j"], src["test_r"])
+    job = Job(w, P, dv, dev, E)
+    m, p = job.m, job.p
 
     def job_e2e():
         src = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
@@ -546,7 +738,7 @@ def run_ours(args, rank, world, local_rank):
         p.V.copy_(src["V0"], non_blocking=True)
         for x in (p.b, p.bh, p.W, p.C):
             x.zero_()
-        return job(src, False)
+        return job.run(src, False, stream)
 
     def barrier():
         if world > 1:
@@ -555,7 +747,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        rmse = job(dv, False)
+        rmse = job.run(dv, False, stream)
     stats = m.training_stats()
     clk = Clocks(local_rank)
     barrier()
@@ -564,13 +756,13 @@ def run_ours(args, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        rmse = job(dv, True)
+        rmse = job.run(dv, True, stream)
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
     launches = launch_count() - l0
     ms_total = ev0.elapsed_time(ev1)
-    epoch_ms = [a.elapsed_time(b) for a, b in epoch_events]
+    epoch_ms = [a.elapsed_time(b) for a, b in job.epoch_events]
     ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     value = replica_throughput(E * nnz, world, ms_step)
@@ -591,49 +783,49 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": replica_throughput(E * nnz, world, ms_e2e), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
 
-    topn = None
+    signatures = topn = None
+    if rank == 0:
+        col_ptr, row, rc = m.csc_from_coo(dv["train_i"], dv["train_j"], dv["train_r"])
+        signatures = measure_signatures(m, col_ptr, row, rc, dv["H"], w)
+        del col_ptr, row, rc
     if rank == 0 and not args.no_serving:
         topn = measure_topn(m, p, w, dev)
-    ingest = serving = generators = batch = None
+    ingest = serving = generators = batch = large = None
     if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
         serving = measure_serving(w, d, P, dev)
         generators = measure_generators(w, d, P, dev)
         batch = measure_batch(dev)
+    m.close()
+    del job, dv, host
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_large and args.workload != "large":
+        large = measure_large(dev)
 
-    peak, peak_kind = peaks()
-    ep_med = float(np.median(epoch_ms))
-    bytes_ep = sgd_bytes_per_epoch(stats, w)
-    achieved = bytes_ep / (ep_med / 1e3) / 1e9
-    prof = traffic_from_profile(kernel_hash())
-    traffic = None
-    if prof is not None:
-        traffic = prof["dram_bytes_per_launch"]
-    roof = {"bound": "hbm", "kernel": "k_sgd_stratum (one epoch = P launches)", "achieved": round(achieved, 1),
-            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": traffic, "algorithmic_bytes_per_epoch": int(bytes_ep), "launches_per_epoch": P,
-            "algorithmic_bytes_per_launch": int(bytes_ep / P),
-            "min_bytes_per_epoch": int(sgd_min_bytes_per_epoch(stats, w)),
-            "min_bytes_achieved_gbs": round(sgd_min_bytes_per_epoch(stats, w) / (ep_med / 1e3) / 1e9, 1),
-            "epoch_ms_median": round(ep_med, 3), "note": f"frac of {peak_kind} HBM copy bandwidth"}
-
+    roof = sgd_roofline(stats, w, epoch_ms, P)
     out = {"metric": "SGD rating-updates/s per epoch at RMSE parity (whole training job)", "value": value,
            "unit": "rating-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 (SGD), int32/int64 (simLSH)", "data": "synthetic (seeded generator, Netflix-shaped)",
+           "dtype": "f32 (SGD), int32/int64 (simLSH)", "data": "synthetic (seeded generator, %s)" % w.name,
            "config": {"workload": w.name, "M": w.M, "N": w.N, "nnz_train": nnz, "F": w.F, "K": w.K, "L": w.L,
                       "bits": w.bits, "psi_pow": w.psi_pow, "epochs": E, "P": P,
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-           "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (ep_med / 1e3),
+           "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (float(np.median(epoch_ms)) / 1e3),
            "epoch_ms_first_and_later": [None if v is None else round(v, 3) for v in epoch_split(epoch_ms, E)],
-           "layout": stats,
+           "layout": stats, "signatures": signatures,
            "topn": topn, "ingest": ingest, "serving": serving, "generators": generators, "batch": batch,
-           "generate_s": round(gen_s, 1)}
+           "large": large, "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(w, sample_frac=0.005)
+        ws = synth.scaled(w, 0.005)
+        ds = synth.generate(ws)
+        cb = cpu_baseline(ws, ds)
+        out["cpu_baseline"] = cb
+        out["rmse_parity"] = rmse_parity(gpu_job_rmse(ws, ds, dev, P), cb["rmse_heldout"], cb["sample"])
+        if not out["rmse_parity"]["pass"]:
+            out["parity_note"] = "RMSE parity FAILED on the sample: the value is not at RMSE parity"
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -641,14 +833,10 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def cpu_baseline(w, sample_frac):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
-    workload: the same shape (N, F, K, L, bits, epochs) with users and ratings
-    scaled by `sample_frac`; the whole job (signatures, top-K, all epochs)."""
+def oracle_job(ws, d):
+    """The FP64 oracle's whole job on workload `ws`: CSC, signatures, top-K, every epoch, held-out RMSE."""
     import oracle
-    import synth
-    ws = synth.scaled(w, sample_frac)
-    d = synth.generate(ws)
+
     t0 = time.time()
     col_ptr, row, r = oracle.csc(ws.M, ws.N, d["train_i"], d["train_j"], d["train_r"])
     sig = oracle.signatures(ws.M, ws.N, ws.L, ws.bits, ws.psi_pow, col_ptr, row, r, d["H"])
@@ -664,10 +852,46 @@ def cpu_baseline(w, sample_frac):
     rm = oracle.rmse(cfg, d["train_i"], d["train_j"], d["train_r"], nbr, mu, po, d["test_i"], d["test_j"], d["test_r"])
     total = time.time() - t0
     nnz = len(d["train_i"])
-    return {"value": ws.epochs * nnz / total, "unit": "rating-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{ws.name}: {ws.M} users x {ws.N} items, {nnz} training ratings, whole job "
-                      f"({ws.epochs} epochs) in {total:.1f} s",
-            "epoch_rating_updates_per_s": nnz / t_ep, "neighbour_build_s": round(t_nb, 2), "rmse_heldout": rm}
+    return {"value": ws.epochs * nnz / total, "total_s": total, "epoch_rating_updates_per_s": nnz / t_ep,
+            "neighbour_build_s": round(t_nb, 2), "rmse_heldout": rm, "U": po.U}
+
+
+def cpu_baseline(ws, d, serial_leg=True):
+    """The FP64 oracle as it stands on a bounded sample `ws` of the workload (same N, F, K, L, bits and
+    epochs; users and ratings scaled down), whole job, in two legs: one host thread, and every host
+    core (OpenMP over the items of Eq. (3) and the blocks of a stratum; bit-identical results)."""
+    import oracle
+
+    info = host_info()
+    nproc = info["nproc"] or 1
+    prev = oracle.set_threads(1)
+    try:
+        serial = oracle_job(ws, d) if serial_leg else None
+        oracle.set_threads(nproc)
+        multi = oracle_job(ws, d)
+    finally:
+        oracle.set_threads(prev)
+    if serial is None:
+        multi.pop("U")
+        nnz = len(d["train_i"])
+        return {"value": multi["value"], "unit": "rating-updates/s", "cores": nproc, "kind": "oracle",
+                "sample": f"{ws.name}: {ws.M} users x {ws.N} items, {nnz} training ratings, whole job "
+                          f"({ws.epochs} epochs) in {multi['total_s']:.1f} s on {nproc} cores",
+                "cpu_model": info["cpu_model"], "nproc": nproc,
+                "epoch_rating_updates_per_s": multi["epoch_rating_updates_per_s"],
+                "neighbour_build_s": multi["neighbour_build_s"], "rmse_heldout": multi["rmse_heldout"]}
+    same = bool(np.array_equal(serial.pop("U"), multi.pop("U")))
+    nnz = len(d["train_i"])
+    sample = (f"{ws.name}: {ws.M} users x {ws.N} items, {nnz} training ratings, whole job ({ws.epochs} epochs) "
+              f"in {serial['total_s']:.1f} s on 1 core, {multi['total_s']:.1f} s on {nproc}")
+    return {"value": multi["value"], "unit": "rating-updates/s", "cores": nproc, "kind": "oracle", "sample": sample,
+            "cpu_model": info["cpu_model"], "nproc": nproc,
+            "epoch_rating_updates_per_s": multi["epoch_rating_updates_per_s"],
+            "neighbour_build_s": multi["neighbour_build_s"], "rmse_heldout": multi["rmse_heldout"],
+            "serial": {"value": serial["value"], "cores": 1,
+                       "epoch_rating_updates_per_s": serial["epoch_rating_updates_per_s"],
+                       "neighbour_build_s": serial["neighbour_build_s"]},
+            "all_core_equals_serial": same}
 
 
 def run_reference(args, rank, world):
@@ -675,12 +899,14 @@ def run_reference(args, rank, world):
         return
     import synth
     w = synth.WORKLOADS[args.workload]
+    ws = synth.scaled(w, 0.002)
+    ds = synth.generate(ws)
     res = []
     for _ in range(args.warmup):
-        cpu_baseline(w, 0.002)
+        cpu_baseline(ws, ds, serial_leg=False)
     t0 = time.time()
     for _ in range(args.steps):
-        res.append(cpu_baseline(w, 0.002))
+        res.append(cpu_baseline(ws, ds, serial_leg=False))
     total = time.time() - t0
     v = float(np.mean([r["value"] for r in res]))
     cb = dict(res[-1])
@@ -688,7 +914,7 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": "SGD rating-updates/s per epoch at RMSE parity (whole training job)",
            "value": v, "unit": "rating-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, Netflix-shaped)",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, %s)" % w.name,
            "config": {"workload": w.name, "sample": cb["sample"]}, "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "rating-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

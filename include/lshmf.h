@@ -103,6 +103,28 @@ lshmf_status lshmf_check(lshmf_handle *h, void *stream);
 /* Number of kernels this library has launched in this process (all handles). */
 int64_t lshmf_launch_count(void);
 
+/* Per-handle options (no counterpart in the paper: resource control and
+ * failure testing).  EINVAL on an unknown option or a value out of range.
+ *  LSHMF_OPT_MEMORY_LIMIT  bytes of device memory the handle's own buffers may
+ *      hold (0 = no limit beyond free memory).  A call whose buffers would
+ *      exceed it returns LSHMF_ENOMEM before launching anything.
+ *  LSHMF_OPT_WAIT_POLLS    polls after which a device-side wait of the SGD
+ *      kernel gives up (0 = the default, over a second per wait); a wait that
+ *      gives up makes the kernel return and the next synchronising call report
+ *      LSHMF_ETIMEOUT.  Range [0, 2^30].
+ *  LSHMF_OPT_SGD_SLOTS     blocks of the schedule held at once by one CTA of the
+ *      SGD kernel (0 = as many as fit in shared memory, at most 4).  The result
+ *      does not depend on it.
+ *  LSHMF_OPT_TEST_WITHHOLD test hook, 1 = the SGD kernel never announces that its
+ *      first finished block of the epoch is done, so every block that waits for
+ *      it runs out its wait (with a small LSHMF_OPT_WAIT_POLLS this returns
+ *      LSHMF_ETIMEOUT quickly); 0 = off.  The parameters are then undefined. */
+#define LSHMF_OPT_MEMORY_LIMIT 1
+#define LSHMF_OPT_WAIT_POLLS 2
+#define LSHMF_OPT_SGD_SLOTS 3
+#define LSHMF_OPT_TEST_WITHHOLD 4
+lshmf_status lshmf_set_option(lshmf_handle *h, int32_t option, int64_t value);
+
 /* Item-major (CSC) layout of a rating set: Sec. 4.1 computes each item's hash
  * from the ratings of its raters.  Input: nnz triples (d_i[p] user in [0, M),
  * d_j[p] item in [0, N), d_r[p] rating), any order, no duplicate (i, j).
@@ -128,6 +150,15 @@ lshmf_status lshmf_csc_from_coo(lshmf_handle *h, const int32_t *d_i, const int32
 lshmf_status lshmf_build_neighbours(lshmf_handle *h, const int64_t *d_col_ptr, const int32_t *d_row,
                                     const uint8_t *d_rc, int64_t nnz, const uint64_t *d_H,
                                     int32_t *d_nbr, uint32_t *d_sig, void *stream);
+
+/* The signature stage of lshmf_build_neighbours alone (Sec. 4.1, Eq. 3): the
+ * keys of all items, d_sig [L x N] uint32 (key of table t, item j at
+ * d_sig[t * N + j]), from the same inputs, with the same validation (EINVAL)
+ * and the same kept pre-sign sums (so lshmf_ingest may follow).  No buckets
+ * and no J^K.  Asynchronous except for the CSC check. */
+lshmf_status lshmf_signatures(lshmf_handle *h, const int64_t *d_col_ptr, const int32_t *d_row,
+                              const uint8_t *d_rc, int64_t nnz, const uint64_t *d_H, uint32_t *d_sig,
+                              void *stream);
 
 /* Top-K generators the paper compares with simLSH (Sec. 5.3, table of the
  * optimal RMSE and overhead of the top-K methods).  `generator` selects:
@@ -291,8 +322,11 @@ lshmf_status lshmf_rmse(lshmf_handle *h, const lshmf_params *p, const int32_t *d
  * 1 <= n <= 33,554,432 query pairs; larger n returns LSHMF_EINVAL.  The
  * first call on a device looks up the array's device address (the device
  * must be current and be the handle's device); make that first call before
- * any stream capture.  All calls share the array, so calls that overlap on
- * the GPU (other streams, other host threads) race: serialise them.
+ * any stream capture.  The address is kept for the life of the process: after
+ * a cudaDeviceReset (or any other teardown of the device's primary context)
+ * it is stale, so do not use this entry point across a device reset.  All
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them.
  * Synchronous; requires lshmf_prepare_training. */
 lshmf_status lshmf_rmse_noalloc(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users,
                                 const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,

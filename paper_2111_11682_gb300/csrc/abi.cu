@@ -48,10 +48,6 @@ static lshmf_status validate_config(Handle *h, const lshmf_config *c) {
 
 using namespace lshmf;
 
-struct lshmf_handle {
-  Handle h;
-};
-
 static inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
 extern "C" {
@@ -114,6 +110,31 @@ lshmf_status lshmf_check(lshmf_handle *hh, void *stream) {
 
 int64_t lshmf_launch_count(void) { return g_launches.load(); }
 
+lshmf_status lshmf_set_option(lshmf_handle *hh, int32_t option, int64_t value) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  switch (option) {
+    case LSHMF_OPT_MEMORY_LIMIT:
+      if (value < 0) return set_err(h, LSHMF_EINVAL, "set_option: memory limit must be >= 0");
+      h->mem_limit = value;
+      return LSHMF_OK;
+    case LSHMF_OPT_WAIT_POLLS:
+      if (value < 0 || value > (int64_t(1) << 30)) return set_err(h, LSHMF_EINVAL, "set_option: wait polls in [0, 2^30]");
+      h->wait_polls = value;
+      return LSHMF_OK;
+    case LSHMF_OPT_SGD_SLOTS:
+      if (value < 0 || value > 4) return set_err(h, LSHMF_EINVAL, "set_option: SGD block slots in [0, 4]");
+      h->sgd_slots = int32_t(value);
+      return LSHMF_OK;
+    case LSHMF_OPT_TEST_WITHHOLD:
+      if (value < 0 || value > 1) return set_err(h, LSHMF_EINVAL, "set_option: test hook is 0 or 1");
+      h->test_withhold = int32_t(value);
+      return LSHMF_OK;
+    default:
+      return set_err(h, LSHMF_EINVAL, "set_option: unknown option %d", option);
+  }
+}
+
 lshmf_status lshmf_csc_from_coo(lshmf_handle *hh, const int32_t *d_i, const int32_t *d_j, const uint8_t *d_r,
                                 int64_t nnz, int64_t *d_col_ptr, int32_t *d_row, uint8_t *d_rc, void *stream) {
   if (!hh) return LSHMF_EINVAL;
@@ -133,6 +154,16 @@ lshmf_status lshmf_build_neighbours(lshmf_handle *hh, const int64_t *d_col_ptr, 
   if (!d_col_ptr || !d_H || !d_nbr || (nnz > 0 && (!d_row || !d_rc)))
     return set_err(h, LSHMF_EINVAL, "build_neighbours: null pointer");
   return build_neighbours(h, d_col_ptr, d_row, d_rc, nnz, d_H, d_nbr, d_sig, S(stream));
+}
+
+lshmf_status lshmf_signatures(lshmf_handle *hh, const int64_t *d_col_ptr, const int32_t *d_row, const uint8_t *d_rc,
+                              int64_t nnz, const uint64_t *d_H, uint32_t *d_sig, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  Handle *h = &hh->h;
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_err(h, LSHMF_EINVAL, "signatures: nnz out of range");
+  if (!d_col_ptr || !d_H || !d_sig || (nnz > 0 && (!d_row || !d_rc)))
+    return set_err(h, LSHMF_EINVAL, "signatures: null pointer");
+  return build_neighbours(h, d_col_ptr, d_row, d_rc, nnz, d_H, nullptr, d_sig, S(stream));
 }
 
 lshmf_status lshmf_build_neighbours_variant(lshmf_handle *hh, int32_t generator, const int64_t *d_col_ptr,

@@ -16,10 +16,6 @@
 
 #include "common.cuh"
 
-struct lshmf_handle {
-  lshmf::Handle h;
-};
-
 namespace lshmf {
 lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
                           cudaStream_t st);

@@ -96,6 +96,12 @@ struct Handle {
   TrainLayout tl;
   LshState lsh;
   DevBuf ing[8];                // online update scratch
+  // caller options (lshmf_set_option)
+  int64_t mem_limit = 0;        // bytes the handle may hold in its buffers (0 = only free memory limits)
+  int64_t held = 0;             // bytes held in grow-only buffers (ensure)
+  int64_t wait_polls = 0;       // polls before a device-side wait gives up (0 = the kernels' default)
+  int32_t sgd_slots = 0;        // block slots per CTA of the SGD kernel (0 = as many as fit)
+  int32_t test_withhold = 0;    // test hook: the SGD kernel never announces its first finished block
 };
 
 inline lshmf_status cuda_status(Handle *h, cudaError_t e, const char *what) {
@@ -168,3 +174,8 @@ lshmf_status check_range_i32(Handle *h, const int32_t *x, int64_t n, int64_t hi,
 lshmf_status check_device_flag(Handle *h, cudaStream_t st, const char *what);
 
 }  // namespace lshmf
+
+// The opaque handle of include/lshmf.h.
+struct lshmf_handle {
+  lshmf::Handle h;
+};

@@ -50,10 +50,6 @@ lshmf_status scratch_address(lshmf::Handle *h, int dev, double **out) {
 
 }  // namespace
 
-struct lshmf_handle {
-  lshmf::Handle h;
-};
-
 extern "C" lshmf_status lshmf_rmse_noalloc(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users,
                                            const int32_t *d_items, const uint8_t *d_r, int64_t n, double *h_rmse,
                                            void *stream) {

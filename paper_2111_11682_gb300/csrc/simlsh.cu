@@ -601,8 +601,10 @@ __global__ void k_write_rows(const int32_t *class_of, const int32_t *pos_of, con
 
 __global__ void k_set_i64_s(int64_t *p, int64_t v) { *p = v; }
 
-lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc,
-                              int64_t nnz, const uint64_t *H, int32_t *nbr, uint32_t *sig_out, cudaStream_t st) {
+// Keys of Eq. (3) for all items into the handle's key buffer (tmp[0], L x N); the
+// pre-sign sums are kept for the online update.  *sig receives the buffer.
+lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,
+                              const uint64_t *H, uint32_t **sig_buf, cudaStream_t st) {
   const lshmf_config &c = h->cfg;
   const int64_t N = c.N;
   const int nb = c.L * c.bits;
@@ -645,9 +647,19 @@ lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *
   h->lsh.W = W;
   h->lsh.N = N;
   h->lsh.ready = true;
+  *sig_buf = sig;
+  return LSHMF_OK;
+}
+
+lshmf_status build_neighbours(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc,
+                              int64_t nnz, const uint64_t *H, int32_t *nbr, uint32_t *sig_out, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  uint32_t *sig = nullptr;
+  LSHMF_TRY(signatures_stage(h, col_ptr, row, rc, nnz, H, &sig, st));
   if (sig_out)
-    LSHMF_CUDA(h, cudaMemcpyAsync(sig_out, sig, sizeof(uint32_t) * c.L * N, cudaMemcpyDeviceToDevice, st));
-  return topk_from_sig(h, sig, N, nbr, st);
+    LSHMF_CUDA(h, cudaMemcpyAsync(sig_out, sig, sizeof(uint32_t) * c.L * c.N, cudaMemcpyDeviceToDevice, st));
+  if (!nbr) return LSHMF_OK;
+  return topk_from_sig(h, sig, c.N, nbr, st);
 }
 
 // Top-K rows (the neighbour search of Alg. 1) of all N items from their keys sig (L x N),

@@ -23,9 +23,13 @@ lshmf_status set_err(Handle *h, lshmf_status st, const char *fmt, ...) {
 lshmf_status ensure(Handle *h, DevBuf &b, size_t bytes, const char *what) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return LSHMF_OK;
+  if (h->mem_limit > 0 && h->held - int64_t(b.bytes) + int64_t(bytes) > h->mem_limit)
+    return set_err(h, LSHMF_ENOMEM, "%s: %zu bytes requested, the handle's memory limit is %lld (holds %lld)", what,
+                   bytes, (long long)h->mem_limit, (long long)h->held);
   if (b.p) {
     cudaDeviceSynchronize();   // in-flight kernels may still use the old block
     cudaFree(b.p);
+    h->held -= int64_t(b.bytes);
     b.p = nullptr;
     b.bytes = 0;
   }
@@ -40,6 +44,7 @@ lshmf_status ensure(Handle *h, DevBuf &b, size_t bytes, const char *what) {
     return set_err(h, LSHMF_ENOMEM, "%s: cudaMalloc(%zu): %s", what, bytes, cudaGetErrorString(e));
   }
   b.bytes = bytes;
+  h->held += int64_t(bytes);
   return LSHMF_OK;
 }
 

@@ -18,13 +18,14 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE"}
 
 # Every entry point declared in include/lshmf.h.
-SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count",
-           "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_prepare_training", "lshmf_train_epoch",
+SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count", "lshmf_set_option",
+           "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_signatures", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
            "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant",
            "lshmf_batch_create", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
 
 GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
+OPT_MEMORY_LIMIT, OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD = 1, 2, 3, 4
 
 
 class LshmfError(RuntimeError):
@@ -91,8 +92,10 @@ def load(build_if_missing: bool = True):
         "lshmf_last_error": ([P], ctypes.c_char_p),
         "lshmf_check": ([P, P], ctypes.c_int),
         "lshmf_launch_count": ([], I64),
+        "lshmf_set_option": ([P, I32, I64], ctypes.c_int),
         "lshmf_csc_from_coo": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
         "lshmf_build_neighbours": ([P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+        "lshmf_signatures": ([P, P, P, P, I64, P, P, P], ctypes.c_int),
         "lshmf_build_neighbours_variant": ([P, I32, P, P, P, I64, P, I32, ctypes.c_uint64, P, P, P], ctypes.c_int),
         "lshmf_prepare_training": ([P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_train_epoch": ([P, CP, I32, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
@@ -201,6 +204,10 @@ class LshMF:
     def check(self, stream=None):
         self._chk(self.lib.lshmf_check(self.h, _stream(stream)))
 
+    def set_option(self, option: int, value: int):
+        """lshmf_set_option: OPT_MEMORY_LIMIT (bytes), OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD."""
+        self._chk(self.lib.lshmf_set_option(self.h, option, int(value)))
+
     def csc_from_coo(self, i, j, r, stream=None):
         nnz = i.numel()
         dev = i.device
@@ -219,6 +226,14 @@ class LshMF:
         self._chk(self.lib.lshmf_build_neighbours(self.h, _ptr(col_ptr), _ptr(row), _ptr(rc), row.numel(), _ptr(H),
                                                   _ptr(nbr), _ptr(sig), _stream(stream)))
         return (nbr, sig) if want_sig else nbr
+
+    def signatures(self, col_ptr, row, rc, H, sig_out=None, stream=None):
+        """lshmf_signatures: simLSH keys only (Eq. 3), int32 view of uint32 [L, N]."""
+        c = self.cfg
+        sig = sig_out if sig_out is not None else torch.empty((c.L, c.N), dtype=torch.int32, device=row.device)
+        self._chk(self.lib.lshmf_signatures(self.h, _ptr(col_ptr), _ptr(row), _ptr(rc), row.numel(), _ptr(H),
+                                            _ptr(sig), _stream(stream)))
+        return sig
 
     def build_neighbours_variant(self, generator, col_ptr=None, row=None, rc=None, rand=None, p=0, seed=0,
                                  want_sig=False, nbr_out=None, device="cuda", stream=None):

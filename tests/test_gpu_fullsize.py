@@ -8,9 +8,10 @@ the launch configuration the benchmark times, on outputs the oracle can compute 
   - stratum 0 (152 persistent CTAs, the benchmark's kernel): the oracle replays stratum 0 over all
     ratings of the users of user blocks 0-3 (blocks of the others are empty for it); parameters of
     those users and of the items of item blocks 0-3 within 1e-4 x max|oracle| per group;
-  - top-N of 16 users, both modes: scores within 1e-4 (1 + |s|) of the oracle's top-N computed
-    from those users' ratings only (a user's scores depend on its own ratings), every returned
-    item scoring the oracle's score at its position.
+  - top-N of 16 users, both modes, on the parameters after one full epoch (so every term of
+    Eq. (1) is non-zero: biases, W and C have moved): scores within 1e-4 (1 + |s|) of the oracle's
+    top-N computed from those users' ratings only (a user's scores depend on its own ratings),
+    every returned item scoring the oracle's score at its position.
 """
 import numpy as np
 import pytest
@@ -85,9 +86,21 @@ def test_full_stratum0_parity(full):
         assert np.abs(g - o).max() <= 1e-4 * scale, name
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_full_topn(full, mode):
+@pytest.fixture(scope="module")
+def trained(full):
     w, d, m, p, nbr, _ = full
+    q = p.clone()
+    m.train_epoch(q, 0)
+    m.check()
+    for name in ("b", "bh", "W", "C"):
+        assert torch.count_nonzero(getattr(q, name)) > 0, name
+    return q
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_topn(full, trained, mode):
+    w, d, m, _, nbr, _ = full
+    p = trained
     rng = np.random.default_rng(8 + mode)
     cnt = np.bincount(d["train_i"], minlength=w.M)
     users = np.concatenate([np.argsort(-cnt)[:4], rng.choice(w.M, 12, replace=False)]).astype(np.int32)

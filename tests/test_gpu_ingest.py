@@ -55,9 +55,11 @@ def _oracle_sig(w, M, N, i, j, r, H):
     return oracle.signatures(M, N, w.L, w.bits, w.psi_pow, col_ptr, row, rr, H)
 
 
-@pytest.fixture(scope="module")
-def case():
-    w = synth.TINY
+@pytest.fixture(scope="module", params=[0.0, 0.3], ids=["beta0", "beta0.3"])
+def case(request):
+    """The tiny workload, with beta = 0 and with beta = 0.3 (Eq. (7) then changes the rate at every local
+    loop after the first)."""
+    w = replace(synth.TINY, beta=request.param)
     d = synth.generate(w)
     return w, d
 
@@ -78,8 +80,9 @@ def test_ingest_keys_rows_and_local_sgd(case):
     old_rows = nbr[:N_old].clone()
     arrs = _params(w, M, N, 11)
     p = _gpu_params(arrs, mu)
+    loops = 2 if w.beta == 0 else 3
     sig = m.ingest(M - M_old, N - N_old, T(ni, torch.int32), T(nj, torch.int32), T(nr, torch.uint8), H, nbr, p,
-                   local_epochs=2, want_sig=True)
+                   local_epochs=loops, want_sig=True)
     torch.cuda.synchronize()
     assert m.cfg.M == M and m.cfg.N == N
     # keys: a neighbour build over all ratings
@@ -93,7 +96,7 @@ def test_ingest_keys_rows_and_local_sgd(case):
     # local SGD
     cfg = oracle.make_cfg(M, N, w.F, w.K, w.P, w.alpha, w.beta, w.lam, w.rating_scale)
     po = oracle.Params(*(np.array(x, np.float64) for x in arrs))
-    oracle.ingest_sgd(cfg, M_old, N_old, oi, oj, orr, ni, nj, nr, g, mu, po, 2)
+    oracle.ingest_sgd(cfg, M_old, N_old, oi, oj, orr, ni, nj, nr, g, mu, po, loops)
     for name in ("U", "V", "b", "bh", "W", "C"):
         gv = getattr(p, name).cpu().numpy().astype(np.float64)
         ov = getattr(po, name)

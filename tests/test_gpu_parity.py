@@ -91,6 +91,13 @@ def test_signatures_bit_exact(tiny):
     assert np.array_equal(tiny.sig.cpu().numpy().view(np.uint32), tiny.orc_sig)
 
 
+def test_signatures_entry_point_bit_exact(tiny):
+    m = LshMF(config_from_workload(tiny.w))
+    sig = m.signatures(tiny.col_ptr, tiny.row, tiny.rc, tiny.H)
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), tiny.orc_sig)
+    m.close()
+
+
 def test_neighbours_bit_exact(tiny):
     g = tiny.nbr.cpu().numpy()
     assert np.array_equal(g, tiny.orc_nbr)

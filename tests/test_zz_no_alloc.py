@@ -2,10 +2,13 @@
 device memory (a process whose GPU memory a pool allocator reserved up front,
 or a latency-critical loop that must not stall in cudaMalloc/cudaFree).
 
-It is called through the C ABI and compared with lshmf_rmse on two calls in
-a row (the fixed scratch array keeps the previous call's contents, so the
-second call checks that nothing stale leaks in).  This file is collected last
-on purpose.
+It is called through the C ABI and compared with lshmf_rmse: on two calls in
+a row with different parameters, on a call at the stated maximum of query
+pairs followed by a small call (the fixed scratch array keeps the previous
+call's partial sums, so a stale one read by the small call would show), and
+just past the maximum (rejected).  Both entry points sum the same FP64 squared
+errors, grouped differently, so they agree to FP64 rounding.  This file is
+collected last on purpose.
 """
 import ctypes
 
@@ -18,14 +21,26 @@ from paper_2111_11682_gb300 import LshMF, LshmfError, Params, config_from_worklo
 
 pytestmark = pytest.mark.gpu
 
-RMSE_RTOL = 2e-3   # the RMSE tolerance of the parity tests
+FP64_RTOL = 1e-12      # same per-pair terms, different summation grouping
+MAX_PAIRS = 16384 * 2048
 
 
 def _T(a, dt):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
 
 
-def test_rmse_noalloc_matches_rmse_twice():
+def _rmse(m, p, qi, qj, qr, n, noalloc):
+    lib = m.lib
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    cp = p._c()
+    out = ctypes.c_double(-1.0)
+    fn = lib.lshmf_rmse_noalloc if noalloc else lib.lshmf_rmse
+    st = fn(m.h, ctypes.byref(cp), ctypes.c_void_p(qi.data_ptr()), ctypes.c_void_p(qj.data_ptr()),
+            ctypes.c_void_p(qr.data_ptr()), n, ctypes.byref(out), stream)
+    return st, out.value
+
+
+def test_rmse_noalloc_matches_rmse():
     w = synth.TINY
     d = synth.generate(w)
     torch.cuda.set_device(0)
@@ -37,27 +52,31 @@ def test_rmse_noalloc_matches_rmse_twice():
     mu = m.prepare_training(ti, tj, tr, nbr)
     p = Params.from_init(d["U0"], d["V0"], w.K, "cuda:0")
     p.mu = mu
-    lib = m.lib
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for epoch in range(2):                      # two calls in a row, on different parameters
+    n = qi.numel()
+    # two calls in a row, on different parameters
+    for epoch in range(2):
         m.train_epoch(p, epoch)
-        cp = p._c()
-        ref, got = ctypes.c_double(0.0), ctypes.c_double(-1.0)
-        st = lib.lshmf_rmse(m.h, ctypes.byref(cp), ctypes.c_void_p(qi.data_ptr()), ctypes.c_void_p(qj.data_ptr()),
-                            ctypes.c_void_p(qr.data_ptr()), qi.numel(), ctypes.byref(ref), stream)
+        st, ref = _rmse(m, p, qi, qj, qr, n, False)
         assert st == lshmf.OK
-        st = lib.lshmf_rmse_noalloc(m.h, ctypes.byref(cp), ctypes.c_void_p(qi.data_ptr()),
-                                    ctypes.c_void_p(qj.data_ptr()), ctypes.c_void_p(qr.data_ptr()), qi.numel(),
-                                    ctypes.byref(got), stream)
-        assert st == lshmf.OK, lib.lshmf_last_error(m.h)
-        assert got.value > 0 and abs(got.value - ref.value) <= RMSE_RTOL * ref.value, (got.value, ref.value)
-    # beyond the stated maximum of query pairs: rejected before any launch
+        st, got = _rmse(m, p, qi, qj, qr, n, True)
+        assert st == lshmf.OK, m.lib.lshmf_last_error(m.h)
+        assert got > 0 and abs(got - ref) <= FP64_RTOL * ref, (got, ref)
+    # the stated maximum (the held-out pairs repeated), then the small set again: every one of the
+    # 16384 partial sums is written by the large call, and the small call must not read them
+    reps = -(-MAX_PAIRS // n)
+    bi, bj, br = (x.repeat(reps)[:MAX_PAIRS].contiguous() for x in (qi, qj, qr))
+    st, ref_big = _rmse(m, p, bi, bj, br, MAX_PAIRS, False)
+    assert st == lshmf.OK
+    st, got_big = _rmse(m, p, bi, bj, br, MAX_PAIRS, True)
+    assert st == lshmf.OK, m.lib.lshmf_last_error(m.h)
+    assert abs(got_big - ref_big) <= FP64_RTOL * ref_big, (got_big, ref_big)
+    st, ref = _rmse(m, p, qi, qj, qr, n, False)
+    st2, got = _rmse(m, p, qi, qj, qr, n, True)
+    assert st == lshmf.OK and st2 == lshmf.OK
+    assert abs(got - ref) <= FP64_RTOL * ref, (got, ref)
+    # one pair past the maximum: rejected before any launch
     with pytest.raises(LshmfError) as e:
-        lib_n = 16384 * 2048 + 1
-        cp = p._c()
-        out = ctypes.c_double(0.0)
-        m._chk(lib.lshmf_rmse_noalloc(m.h, ctypes.byref(cp), ctypes.c_void_p(qi.data_ptr()),
-                                      ctypes.c_void_p(qj.data_ptr()), ctypes.c_void_p(qr.data_ptr()), lib_n,
-                                      ctypes.byref(out), stream))
+        st, _ = _rmse(m, p, bi, bj, br, MAX_PAIRS + 1, True)
+        m._chk(st)
     assert e.value.status == lshmf.EINVAL
     m.close()
