@@ -72,9 +72,9 @@ typedef struct {
   int32_t bits;         /* 1..32, L * bits <= 1024 */
   int32_t psi_pow;      /* 0..4 */
   int32_t P;            /* 1..4096 */
-  float alpha[6];
-  float beta;
-  float lambda[6];
+  float alpha[6];       /* >= 0, alpha[g] * lambda[g] < 1 */
+  float beta;           /* >= 0 */
+  float lambda[6];      /* >= 0 */
   float rating_scale;   /* > 0 */
 } lshmf_config;
 
@@ -115,10 +115,11 @@ int64_t lshmf_launch_count(void);
  *  LSHMF_OPT_SGD_SLOTS     blocks of the schedule held at once by one CTA of the
  *      SGD kernel (0 = as many as fit in shared memory, at most 4).  The result
  *      does not depend on it.
- *  LSHMF_OPT_TEST_WITHHOLD test hook, 1 = the SGD kernel never announces that its
- *      first finished block of the epoch is done, so every block that waits for
- *      it runs out its wait (with a small LSHMF_OPT_WAIT_POLLS this returns
- *      LSHMF_ETIMEOUT quickly); 0 = off.  The parameters are then undefined. */
+ *  LSHMF_OPT_TEST_WITHHOLD test hook, 1 = the SGD kernel never tells the first
+ *      pipeline of each CTA that the stratum's work is all handed out, so its
+ *      producers wait for a flag that nothing sets until their poll limit runs
+ *      out (with a small LSHMF_OPT_WAIT_POLLS the call returns LSHMF_ETIMEOUT
+ *      quickly); 0 = off.  The parameters are then undefined. */
 #define LSHMF_OPT_MEMORY_LIMIT 1
 #define LSHMF_OPT_WAIT_POLLS 2
 #define LSHMF_OPT_SGD_SLOTS 3

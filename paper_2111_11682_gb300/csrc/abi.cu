@@ -38,9 +38,12 @@ static lshmf_status validate_config(Handle *h, const lshmf_config *c) {
   if (c->P < 1 || c->P > 4096) return set_err(h, LSHMF_EINVAL, "P must be in [1, 4096]");
   if (!(c->rating_scale > 0.f)) return set_err(h, LSHMF_EINVAL, "rating_scale must be > 0");
   if (!(c->beta >= 0.f)) return set_err(h, LSHMF_EINVAL, "beta must be >= 0");
-  for (int g = 0; g < 6; ++g)
+  for (int g = 0; g < 6; ++g) {
     if (!(c->alpha[g] >= 0.f) || !(c->lambda[g] >= 0.f))
       return set_err(h, LSHMF_EINVAL, "alpha and lambda must be >= 0");
+    if (!(double(c->alpha[g]) * double(c->lambda[g]) < 1.0))
+      return set_err(h, LSHMF_EINVAL, "alpha * lambda must be < 1 (a larger step reverses the parameter's sign)");
+  }
   return LSHMF_OK;
 }
 
@@ -94,7 +97,7 @@ void lshmf_destroy(lshmf_handle *hh) {
   TrainLayout &t = h->tl;
   DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                     &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
-                          &t.seg_ck, &t.ck_roff, &t.next_blk};
+                          &t.seg_ck, &t.ck_roff, &t.df};
   for (DevBuf *b : bufs) release(*b);
   cudaFree(h->d_err);
   cudaFree(h->d_red);
@@ -245,7 +248,7 @@ lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out
   for (const auto &b : h->prep) bytes += b.bytes;
   const DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                           &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
-                          &t.seg_ck, &t.ck_roff, &t.next_blk};
+                          &t.seg_ck, &t.ck_roff, &t.df};
   for (const DevBuf *b : bufs) bytes += b->bytes;
   for (const auto &b : h->ing) bytes += b.bytes;
   out->device_bytes = bytes + h->red_part.bytes + h->lsh.sums.bytes + h->aux.bytes;

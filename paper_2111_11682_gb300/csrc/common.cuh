@@ -65,7 +65,7 @@ struct TrainLayout {
   DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
   DevBuf seg_ck;    // int32  [nseg + 1]: first chunk of each run (chunks of SGD_CH ratings)
   DevBuf ck_roff;   // int64  [chunks]: offset of each chunk's packed neighbour values
-  DevBuf next_blk;  // int32  [P]: blocks of each stratum taken so far (SGD scheduler)
+  DevBuf df;        // int32  [P]: blocks of each stratum taken so far (SGD scheduler)
   int64_t nchunks = 0;
 };
 

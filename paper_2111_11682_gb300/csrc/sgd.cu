@@ -44,8 +44,9 @@
 // Progress.  Segments are handed out in block order, each group's in that
 // order, chunks are prepared and run in stream order, and a chunk waits only
 // for ratings of earlier segments of its block.  The oldest unfinished segment
-// of a CTA therefore never waits on a user, and every wait is bounded: after SGD_SPIN_LIMIT polls the kernel
-// records a timeout, raises the CTA's abort flag and returns.
+// of a CTA therefore never waits on a user, and every wait is bounded: after the handle's poll limit
+// (LSHMF_OPT_WAIT_POLLS; by default over a second) the kernel records a timeout, raises the CTA's abort
+// flag, waits for its own copies in flight and returns.
 #include <cuda/atomic>
 
 #include <algorithm>
@@ -55,8 +56,7 @@
 
 namespace lshmf {
 
-constexpr int SGD_SPIN_LIMIT = 1 << 22;   // polls of a bounded spin (with back-off: well over a second)
-constexpr int SGD_WAIT_TRIES = 1 << 20;   // suspended tries of a bounded mbarrier wait
+constexpr int64_t SGD_DEFAULT_POLLS = int64_t(1) << 22;   // polls of a bounded spin (with back-off: over a second)
 constexpr unsigned SGD_SUSPEND_NS = 1000; // suspend-time hint of one try
 constexpr int CH = SGD_CH;    // ratings per chunk (the chunk layout of prepare_training uses the same size)
 constexpr int GP = 3;         // producer warps per group
@@ -83,6 +83,9 @@ struct SgdArgs {
   const int64_t *blk_user;
   const int32_t *order;
   int32_t *next_blk;         // per stratum: blocks taken (zeroed per epoch)
+  int64_t polls;             // bounded-wait limit (spins)
+  int64_t tries;             // bounded-wait limit (suspending mbarrier tries)
+  int withhold;              // test hook: group 0 is never told that the stratum's segments are all handed out
   const int32_t *users;
   const float *bh0n;
   double *seg_sq;
@@ -245,7 +248,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
 __device__ __forceinline__ bool mbar_wait(const SgdArgs &a, uint64_t *bar, unsigned parity, CtaCtl *ctl) {
   int it = 0;
   while (!mbar_try(bar, parity)) {
-    if (++it > SGD_WAIT_TRIES || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
+    if (++it > a.tries || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
   }
   return true;
 }
@@ -257,7 +260,7 @@ __device__ __forceinline__ bool lock_warp(const SgdArgs &a, int *l, CtaCtl *ctl)
     if ((threadIdx.x & 31) == 0) ok = atomicCAS(l, 0, 1) == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) break;
-    if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
+    if (++it > a.polls || ld_acq(&ctl->abort_)) return sgd_abort(a, ctl);
     backoff(it);
   }
   __threadfence_block();
@@ -308,7 +311,7 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<F
       }
       slot = __shfl_sync(0xffffffffu, slot, 0);
       if (slot >= 0) break;
-      if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+      if (++it > a.polls || ld_acq(&ctl->abort_)) {
         sgd_abort(a, ctl);
         return;
       }
@@ -364,7 +367,7 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<F
               }
             }
             if (g >= 0) break;
-            if (++wait > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+            if (++wait > a.polls || ld_acq(&ctl->abort_)) {
               ok = false;
               break;
             }
@@ -389,7 +392,7 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<F
     return;
   }
   if (lane == 0)
-    for (int h = 0; h < ng; ++h) st_rel(&grp[h].done, 1);
+    for (int h = a.withhold ? 1 : 0; h < ng; ++h) st_rel(&grp[h].done, 1);
 }
 
 // ------------------------------------------------------------- producer ----
@@ -415,7 +418,7 @@ struct Producer {
       const int d = ld_acq(&G.done);
       if (pos < ld_acq(&G.endpos)) return 1;
       if (d) return 0;
-      if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+      if (++it > a.polls || ld_acq(&ctl->abort_)) {
         sgd_abort(a, ctl);
         return -1;
       }
@@ -497,7 +500,7 @@ struct Producer {
       const bool need = lane < n && rank > 0;
       int it = 0;
       while (__any_sync(0xffffffffu, need && ld_acq(&cn[us]) != rank)) {
-        if (++it > SGD_SPIN_LIMIT || ld_acq(&ctl->abort_)) {
+        if (++it > a.polls || ld_acq(&ctl->abort_)) {
           cp_async_wait_all();
           return sgd_abort(a, ctl);
         }
@@ -896,7 +899,7 @@ static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream
   auto need = [&](int ng, int ns) {
     return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + 2 * sizeof(int) * size_t(ns) * a.maxu;
   };
-  int ng = MAX_GROUPS, ns = MAX_SLOTS;
+  int ng = MAX_GROUPS, ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : MAX_SLOTS;
   while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
   while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
   if (need(ng, ns) > size_t(h->smem_optin))
@@ -928,7 +931,7 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.N * c.K, 256), 16L * h->num_sms));
   LSHMF_LAUNCH(h, k_gather_bh0n, g, 256, 0, st, tl.bh0.as<float>(), tl.nbr.as<int32_t>(), c.N * c.K,
                tl.bh0n.as<float>());
-  LSHMF_CUDA(h, cudaMemsetAsync(tl.next_blk.p, 0, size_t(c.P) * 4, st));
+  LSHMF_CUDA(h, cudaMemsetAsync(tl.df.p, 0, size_t(c.P) * 4, st));
   if (h_sq) LSHMF_CUDA(h, cudaMemsetAsync(tl.seg_sq.p, 0, tl.nseg * 8, st));
   SgdArgs a;
   a.sr = tl.sr.as<uint32_t>();
@@ -942,7 +945,7 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   a.blk_seg = tl.blk_seg.as<int64_t>();
   a.blk_user = tl.blk_user.as<int64_t>();
   a.order = tl.blk_order.as<int32_t>();
-  a.next_blk = tl.next_blk.as<int32_t>();
+  a.next_blk = tl.df.as<int32_t>();
   a.users = tl.users.as<int32_t>();
   a.bh0n = tl.bh0n.as<float>();
   a.seg_sq = tl.seg_sq.as<double>();
@@ -968,6 +971,9 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   a.F = c.F; a.K = c.K; a.P = c.P; a.mw = tl.mask_words; a.maxu = std::max(1, tl.max_users_per_block);
   a.nslots = 1;
   a.want_sq = h_sq != nullptr;
+  a.polls = h->wait_polls > 0 ? h->wait_polls : SGD_DEFAULT_POLLS;
+  a.tries = std::max<int64_t>(1, a.polls >> 2);
+  a.withhold = h->test_withhold;
   a.err = h->d_err;
   const int fpl = (c.F + 31) / 32, kpl = (c.K + 31) / 32;
   lshmf_status s;

@@ -1,12 +1,14 @@
 // simLSH neighbour build (Sec. 4.1, Eq. 3, Alg. 1) on sm_103a.
 //
 //   k_coo_keys / radix sort / k_csc_emit   rating triples -> item-major CSC
-//   k_sig_units + k_sig_finalize           signatures: for every (item j,
+//   k_sig_units + k_sig_main + k_sig_finalize   signatures: for every (item j,
 //       table t, bit g) the integer sum  sum_i Psi(r_ij) * (2 H_i[t,g] - 1),
 //       Upsilon(s) = [s >= 0].  A warp owns one work unit (a whole light item
-//       or a 4096-rating chunk of a heavy one); lane l owns hash bits l, l+32,
-//       ... of every word, so one broadcast load of H_i's words feeds all
-//       lanes; Psi * bit is accumulated exactly in int32 or int64.
+//       or a 4096-rating chunk of a heavy one) and takes it 32 ratings at a
+//       time, a rating per lane: a warp bit transpose of each 32-bit word of
+//       the raters' hash bits gives lane l the raters holding bit l, and nibble
+//       tables of their Psi values turn that mask into the exact weighted sum
+//       (int32 or int64; heavy items merge their chunks by integer atomics).
 //   classes of identical keys              items whose L keys all agree have
 //       equal collision counts with everyone; they are grouped (hash sort with
 //       an exact equality check) so top-K work is per class, not per item.
@@ -163,13 +165,42 @@ __device__ __forceinline__ void emit_keys(const bool (&bit)[2 * W], int64_t j, i
   }
 }
 
-template <int W, class ACC>
+// 32 x 32 bit transpose across the warp: on entry bit c of lane r's word is
+// M[r][c]; on return bit r of lane c's word is M[r][c] (five butterfly rounds
+// that swap the off-diagonal sub-blocks of halving size).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int x = 0; x < 5; ++x) {
+    const int j = 16 >> x;
+    const uint32_t m = masks[x];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) ? ((v & ~m) | ((y >> j) & m)) : ((v & m) | ((y << j) & ~m));
+  }
+  return v;
+}
+
+// Eq. (3) for one work unit per warp (a whole light item or a SIG_CHUNK-rating
+// chunk of a heavy one), 32 ratings at a time, lane k holding rating k:
+//   - lane k loads its rating's user i_k, Psi(r_k) and the W words of H_{i_k};
+//   - the warp writes 8 nibble tables, tab[q][m] = sum of Psi(r_{4q+k}) over the
+//     bits k of m (k < 4);
+//   - for each 32-bit half-word h of the hash bits, a warp transpose gives lane l
+//     the mask of the ratings whose bit 32 h + l is set, and the 8 nibbles of
+//     that mask index the tables: lane l adds sum over the ratings with the bit
+//     set of Psi(r) -- the integer sum of Eq. (3) without its sign, exact in TAB
+//     (at most 32 Psi per batch) and accumulated in ACC.
+// Lane l ends with sum_k Psi(r_k) H_{i_k}[bit] for bits 64 (s >> 1) + 32 (s & 1) + l
+// (slot s < 2W); the pre-sign sum is 2 * that - sum_k Psi(r_k).
+template <int W, class ACC, class TAB>
 __global__ void __launch_bounds__(32 * SIG_WARPS)
 k_sig_main(const int64_t *col_ptr, const int32_t *row, const uint8_t *r, const uint64_t *H,
            int hstride, int64_t N, int L, int bits, int psi_pow, const int64_t *unit_start, int64_t nunits,
            const int64_t *split_idx, ACC *acc, uint32_t *sig, int64_t *sums) {
-  const int lane = threadIdx.x & 31;
-  const int64_t u = int64_t(blockIdx.x) * SIG_WARPS + (threadIdx.x >> 5);
+  __shared__ TAB tabs[SIG_WARPS][8][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t u = int64_t(blockIdx.x) * SIG_WARPS + warp;
   if (u >= nunits) return;
   // item of this unit: last j with unit_start[j] <= u
   int64_t lo = 0, hi = N;
@@ -183,32 +214,49 @@ k_sig_main(const int64_t *col_ptr, const int32_t *row, const uint8_t *r, const u
   const int64_t c0 = col_ptr[j], c1 = col_ptr[j + 1];
   const int64_t p0 = c0 + sub * SIG_CHUNK;
   const int64_t p1 = min(c1, p0 + SIG_CHUNK);
+  TAB(*tab)[16] = tabs[warp];
   ACC a[2 * W];
 #pragma unroll
   for (int s = 0; s < 2 * W; ++s) a[s] = 0;
   ACC tot = 0;
+  const int q = lane >> 2, a2 = lane & 3;
   for (int64_t base = p0; base < p1; base += 32) {
     const int64_t p = base + lane;
-    int32_t myi = 0;
-    ACC myps = 0;
-    if (p < p1) {
-      myi = __ldg(row + p);
-      myps = psi_of<ACC>(__ldg(r + p), psi_pow);
-    }
-    const int n = int(min(int64_t(32), p1 - base));
-    for (int e = 0; e < n; ++e) {
-      const int32_t i = __shfl_sync(0xffffffffu, myi, e);
-      const ACC ps = __shfl_sync(0xffffffffu, myps, e);
-      const uint64_t *hr = H + int64_t(i) * hstride;
+    const bool valid = p < p1;
+    const int32_t i = valid ? __ldg(row + p) : 0;
+    const TAB ps = valid ? psi_of<TAB>(__ldg(r + p), psi_pow) : TAB(0);
+    uint32_t hw[2 * W];
+    const uint64_t *hr = H + int64_t(i) * hstride;
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const uint64_t hw = w < hstride ? __ldg(hr + w) : 0ull;
-        a[2 * w] += ACC((hw >> lane) & 1u) * ps;
-        a[2 * w + 1] += ACC((hw >> (32 + lane)) & 1u) * ps;
-      }
-      tot += ps;
+    for (int w = 0; w < W; ++w) {
+      const uint64_t x = (valid && w < hstride) ? __ldg(hr + w) : 0ull;
+      hw[2 * w] = uint32_t(x);
+      hw[2 * w + 1] = uint32_t(x >> 32);
     }
+    tot += ACC(ps);
+    // nibble tables: lane l writes entries 4 a2 .. 4 a2 + 3 of table q = l >> 2
+    {
+      const TAB x0 = __shfl_sync(0xffffffffu, ps, 4 * q), x1 = __shfl_sync(0xffffffffu, ps, 4 * q + 1);
+      const TAB x2 = __shfl_sync(0xffffffffu, ps, 4 * q + 2), x3 = __shfl_sync(0xffffffffu, ps, 4 * q + 3);
+      const TAB b = ((a2 & 1) ? x2 : TAB(0)) + ((a2 & 2) ? x3 : TAB(0));
+      tab[q][4 * a2] = b;
+      tab[q][4 * a2 + 1] = b + x0;
+      tab[q][4 * a2 + 2] = b + x1;
+      tab[q][4 * a2 + 3] = b + x0 + x1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2 * W; ++s) {
+      const uint32_t m = warp_transpose32(hw[s]);
+      TAB sum = 0;
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) sum += tab[qq][(m >> (4 * qq)) & 15u];
+      a[s] += ACC(sum);
+    }
+    __syncwarp();   // the tables are rewritten by the next batch
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   if (nsub == 1) {
     bool bit[2 * W];
 #pragma unroll
@@ -272,7 +320,7 @@ lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, ui
   return LSHMF_OK;
 }
 
-template <int W, class ACC>
+template <int W, class ACC, class TAB>
 static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
                                    const uint64_t *H, const int64_t *unit_start, int64_t nunits,
                                    const int64_t *split_idx, int64_t nsplit, uint32_t *sig, int64_t *sums,
@@ -282,7 +330,7 @@ static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int3
   LSHMF_TRY(ensure(h, h->tmp[4], accn * sizeof(ACC), "signature accumulators"));
   ACC *acc = h->tmp[4].as<ACC>();
   LSHMF_CUDA(h, cudaMemsetAsync(acc, 0, accn * sizeof(ACC), st));
-  LSHMF_LAUNCH(h, (k_sig_main<W, ACC>), (unsigned)ceil_div(nunits, SIG_WARPS), 32 * SIG_WARPS, 0, st,
+  LSHMF_LAUNCH(h, (k_sig_main<W, ACC, TAB>), (unsigned)ceil_div(nunits, SIG_WARPS), 32 * SIG_WARPS, 0, st,
                col_ptr, row, r, H, (c.L * c.bits + 63) / 64, c.N, c.L, c.bits, c.psi_pow, unit_start, nunits,
                split_idx, acc, sig, sums);
   if (nsplit > 0)
@@ -291,17 +339,17 @@ static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int3
   return LSHMF_OK;
 }
 
-template <class ACC>
+template <class ACC, class TAB>
 static lshmf_status dispatch_sig(Handle *h, int W, const int64_t *col_ptr, const int32_t *row,
                                  const uint8_t *r, const uint64_t *H, const int64_t *us, int64_t nu,
                                  const int64_t *si, int64_t ns, uint32_t *sig, int64_t *sums, cudaStream_t st) {
   switch (W) {
-    case 1: return run_signatures<1, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 2: return run_signatures<2, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 3: return run_signatures<3, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 4: return run_signatures<4, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 8: return run_signatures<8, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 16: return run_signatures<16, ACC>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 1: return run_signatures<1, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 2: return run_signatures<2, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 3: return run_signatures<3, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 4: return run_signatures<4, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 8: return run_signatures<8, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 16: return run_signatures<16, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
     default: return set_err(h, LSHMF_EINVAL, "internal: unsupported padded word count %d", W);
   }
 }
@@ -630,9 +678,10 @@ lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *
   LSHMF_CUDA(h, cudaMemcpyAsync(&nunits, unit_start + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   LSHMF_CUDA(h, cudaMemcpyAsync(&nsplit, split_idx + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   LSHMF_CUDA(h, cudaStreamSynchronize(st));
-  double bound = 1.0;
-  for (int q = 0; q < c.psi_pow; ++q) bound *= double(hb[1]);
-  bound *= 2.0 * double(std::max<int64_t>(1, hb[0]));
+  double psimax = 1.0;
+  for (int q = 0; q < c.psi_pow; ++q) psimax *= double(hb[1]);
+  const double bound = psimax * 2.0 * double(std::max<int64_t>(1, hb[0]));
+  const bool tab64 = 32.0 * psimax >= 4294967296.0;   // a batch of 32 Psi values overflows uint32
   // --- signatures into tmp sig buffer (L x N); the handle keeps the pre-sign sums
   // (N x 64W, int64) for the online update (Sec. 4.3)
   LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * N + 16, "signatures"));
@@ -640,10 +689,15 @@ lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *
   h->lsh.ready = false;
   LSHMF_TRY(ensure(h, h->lsh.sums, sizeof(int64_t) * 64 * W * N, "kept signature sums"));
   int64_t *sums = h->lsh.sums.as<int64_t>();
-  if (bound < 2147483647.0)
-    LSHMF_TRY(dispatch_sig<int32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, sums, st));
+  if (bound < 2147483647.0 && !tab64)
+    LSHMF_TRY((dispatch_sig<int32_t, uint32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                               sums, st)));
+  else if (!tab64)
+    LSHMF_TRY((dispatch_sig<int64_t, uint32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                               sums, st)));
   else
-    LSHMF_TRY(dispatch_sig<int64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig, sums, st));
+    LSHMF_TRY((dispatch_sig<int64_t, uint64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                               sums, st)));
   h->lsh.W = W;
   h->lsh.N = N;
   h->lsh.ready = true;

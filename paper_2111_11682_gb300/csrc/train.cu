@@ -9,13 +9,13 @@
 //   rating, a K-bit mask (bit k: J^K[j][k] in R(i)) and, packed per rating,
 //   the ratings r_{i, J^K[j][k]} of the set bits.
 //
-// Stratum kernel: one CTA per block of the stratum.  Warps take the block's
-// item segments in item order (item parameters v_j, bhat_j, w_j, c_j held in
-// registers as in Alg. 3); a rating waits until its user's previous ratings in
-// the block (smaller items) are done, tracked by per-user counters in shared
-// memory.  Every rating therefore reads exactly the values the sequential
-// (j, i) order would give it: the result is that of the sequential schedule,
-// and independent of warp timing.
+// SGD epoch (sgd.cu): one launch per stratum; a CTA's scheduler warp takes the
+// stratum's blocks from a counter and hands their item runs, cut into chunks
+// of SGD_CH ratings, to its groups of warps; a chunk's users must have finished
+// their earlier ratings of the block (per-user counters in shared memory).
+// Every rating therefore reads exactly the values the sequential
+// (stratum, block, j, i) order would give it: the result is that of the
+// sequential schedule, and independent of timing.
 #include <cuda/atomic>
 
 #include <algorithm>
@@ -326,8 +326,6 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   const size_t ismem = wide ? size_t((N + 31) / 32) * 4 : size_t(N) * 2;
   if (ismem > 200 * 1024)
     return set_err(h, LSHMF_EINVAL, "prepare_training: N = %lld too large for the index map", (long long)N);
-  LSHMF_TRY(check_range_i32(h, d_nbr, N * c.K, N, st, "prepare_training (J^K entries)"));
-  LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
   const unsigned g = grid_for(h, nnz);
   const int64_t n1 = nnz + 1;
   // named temporaries (grow-only, kept by the handle between calls)
@@ -341,7 +339,21 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
                                  size_t(nnz) * 8, size_t(nnz) * 4,                                   // kU vU
                                  size_t(nnz) * 4, size_t(n1) * 8, size_t(n1) * 8,                    // bposC cnt roff
                                  size_t(NB) * 8, size_t(NB) * 4, size_t(NB) * 8};                    // block order
+  // admission before any launch: the buffers whose sizes are known now must fit the handle's limit
+  if (h->mem_limit > 0) {
+    int64_t grow = 0;
+    for (int q = 0; q < PREP_BUFS; ++q) grow += std::max<int64_t>(0, int64_t(tsz[q] + 64) - int64_t(T[q].bytes));
+    const int64_t known[][2] = {{nnz * 4, int64_t(tl.sr.bytes)}, {nnz, int64_t(tl.rat.bytes)},
+                                {nnz * 4 * ((c.K + 31) / 32), int64_t(tl.mask.bytes)},
+                                {N * c.K * 4, int64_t(tl.nbr.bytes)}, {nnz * 4, int64_t(tl.csr_j.bytes)}};
+    for (const auto &k : known) grow += std::max<int64_t>(0, k[0] - k[1]);
+    if (h->held + grow > h->mem_limit)
+      return set_err(h, LSHMF_ENOMEM, "prepare_training: needs at least %lld more bytes, the handle's memory limit is "
+                     "%lld (holds %lld)", (long long)grow, (long long)h->mem_limit, (long long)h->held);
+  }
   for (int q = 0; q < PREP_BUFS; ++q) LSHMF_TRY(ensure(h, T[q], tsz[q] + 64, "prepare temporaries"));
+  LSHMF_TRY(check_range_i32(h, d_nbr, N * c.K, N, st, "prepare_training (J^K entries)"));
+  LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
   uint64_t *k0 = T[0].as<uint64_t>(), *k1 = T[1].as<uint64_t>();
   uint32_t *v0 = T[2].as<uint32_t>(), *v1 = T[3].as<uint32_t>();
   int32_t *iA = T[4].as<int32_t>(), *jA = T[5].as<int32_t>();
@@ -474,7 +486,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
     tl.nchunks = nchunks;
     LSHMF_TRY(ensure(h, tl.seg_ck, (nseg + 1) * 4, "layout run chunks"));
     LSHMF_TRY(ensure(h, tl.ck_roff, nchunks * 8 + 8, "layout chunk offsets"));
-    LSHMF_TRY(ensure(h, tl.next_blk, P * 4, "stratum block counters"));
+    LSHMF_TRY(ensure(h, tl.df, P * 4, "SGD stratum block counters"));
     LSHMF_LAUNCH(h, k_chunks, grid_for(h, nseg + 1), 256, 0, st, tl.seg_p0.as<int64_t>(), ckscan, nseg, roff,
                  tl.seg_ck.as<int32_t>(), tl.ck_roff.as<int64_t>());
   }

@@ -3,7 +3,11 @@
   - LSHMF_ENOMEM: a per-handle memory limit (LSHMF_OPT_MEMORY_LIMIT) below what
     the training layout needs is refused before anything is launched, and the
     handle works again once the limit is lifted.
+  - LSHMF_ETIMEOUT: a bounded device wait on a flag that nothing sets (the
+    LSHMF_OPT_TEST_WITHHOLD hook) runs out under a small poll limit; the kernel
+    returns, the status reaches the host and the handle recovers.
   - Bad option values are rejected (EINVAL).
+  - The number of block slots per CTA of the SGD kernel does not change the result.
 """
 import numpy as np
 import pytest
@@ -62,4 +66,53 @@ def test_bad_option_values_are_rejected(tiny):
         with pytest.raises(LshmfError) as e:
             m.set_option(opt, val)
         assert e.value.status == lshmf.EINVAL
+    m.close()
+
+
+def _train(m, tiny, epochs=1):
+    mu = m.prepare_training(tiny["ti"], tiny["tj"], tiny["tr"], tiny["nbr"])
+    p = Params.from_init(tiny["d"]["U0"], tiny["d"]["V0"], tiny["w"].K, "cuda:0")
+    p.mu = mu
+    for e in range(epochs):
+        m.train_epoch(p, e)
+    return p
+
+
+def test_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(tiny):
+    """The test hook withholds the end-of-stratum flag from the first pipeline of every CTA, so its
+    producers wait for a flag nothing sets; with a poll limit of 2,000 their waits run out in well
+    under a second, the kernel returns, and the next synchronising call reports LSHMF_ETIMEOUT.  The
+    handle then trains normally again after a new prepare."""
+    import time
+
+    m = LshMF(config_from_workload(tiny["w"]))
+    ref = _train(m, tiny)
+    m.check()
+    m.set_option(OPT_WAIT_POLLS, 2000)
+    m.set_option(OPT_TEST_WITHHOLD, 1)
+    t0 = time.time()
+    with pytest.raises(LshmfError) as e:
+        p = _train(m, tiny)
+        m.check()
+    assert e.value.status == lshmf.ETIMEOUT
+    assert time.time() - t0 < 30.0
+    m.set_option(OPT_TEST_WITHHOLD, 0)
+    m.set_option(OPT_WAIT_POLLS, 0)
+    p = _train(m, tiny)
+    m.check()
+    for name in ("U", "V", "b", "bh", "W", "C"):
+        assert torch.equal(getattr(p, name), getattr(ref, name)), name
+    m.close()
+
+
+@pytest.mark.parametrize("slots", [1, 2, 3])
+def test_block_slots_do_not_change_the_result(tiny, slots):
+    """One to four blocks in flight per CTA: the same parameters, bit for bit, after two epochs."""
+    m = LshMF(config_from_workload(tiny["w"]))
+    ref = _train(m, tiny, 2)
+    m.set_option(OPT_SGD_SLOTS, slots)
+    p = _train(m, tiny, 2)
+    m.check()
+    for name in ("U", "V", "b", "bh", "W", "C"):
+        assert torch.equal(getattr(p, name), getattr(ref, name)), (slots, name)
     m.close()
