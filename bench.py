@@ -325,28 +325,41 @@ def measure_ingest(w, d, P, dev, reps=3, frac=0.01, local_epochs=1):
             "ratings_per_s": n / (ms / 1e3)}
 
 
-def measure_serving(w, d, P, dev, frac=0.01, n_inc=4, rate=4000.0, horizon=2.0, seed=1):
-    """Serving loop (serve.Server) under a Poisson mix: top-N queries of 1-16 users (mode 1,
-    top-10) arrive at `rate` per second for `horizon` seconds, and the last `frac` of users and
-    items arrive as `n_inc` online updates spread over the horizon.  The loop merges waiting
-    queries into one call (continuous batching) and applies updates in arrival order.
-    Latency is host wall clock from submission to answer."""
+def measure_serving(w, d, P, dev, frac_users=0.02, frac_items=0.01, rate=4000.0, horizon=4.0, seed=1):
+    """Serving loop (serve.Server) under a Poisson mix on the workload: top-N queries of 1-16 users
+    (mode 1, top-10) arrive at `rate` per second for `horizon` seconds, and the last `frac_users` of
+    users and `frac_items` of items arrive as online updates of lognormal size (median 20k ratings,
+    clipped to 1k-1M) at uniform random times.  Queries are merged into calls (continuous batching,
+    up to 4 calls in flight on their own streams) and answered from the last published model while
+    updates run on their own thread and stream.  Latency is host wall clock from submission to answer."""
     import dataclasses
     import threading
 
     import torch
 
     from paper_2111_11682_gb300 import LshMF, Params, config_from_workload
-    from paper_2111_11682_gb300.serve import Server, latency_summary, poisson_times
+    from paper_2111_11682_gb300.serve import Server, latency_summary, poisson_times, split_summary
 
-    M_new, N_new = max(n_inc, int(w.M * frac)), max(n_inc, int(w.N * frac))
+    rng = np.random.default_rng(seed)
+    M_new, N_new = int(w.M * frac_users), int(w.N * frac_items)
     M_old, N_old = w.M - M_new, w.N - N_new
-    Mb = [M_old + (k + 1) * M_new // n_inc for k in range(n_inc)]
-    Nb = [N_old + (k + 1) * N_new // n_inc for k in range(n_inc)]
     i, j, r = d["train_i"], d["train_j"], d["train_r"]
-    ku = np.searchsorted(np.array([M_old] + Mb), i, side="right") - 1   # -1: old user
-    kj = np.searchsorted(np.array([N_old] + Nb), j, side="right") - 1
-    kr = np.maximum(ku, kj)
+    # increments: new users in id order cut to lognormal rating counts; new items spread alike
+    per_user = np.bincount(i[i >= M_old] - M_old, minlength=M_new)
+    sizes = []
+    while sum(sizes) < per_user.sum():
+        sizes.append(int(np.clip(rng.lognormal(np.log(20000.0), 1.5), 1000, 1_000_000)))
+    cum_u = np.cumsum(per_user)
+    ku = np.searchsorted(np.cumsum(sizes), cum_u, side="left")      # increment of each new user
+    nk = int(ku.max()) + 1
+    kj_new = (np.arange(N_new) * nk) // max(1, N_new)               # increment of each new item
+    kr = np.full(len(i), -1, np.int64)
+    nu_mask, nj_mask = i >= M_old, j >= N_old
+    kr[nu_mask] = ku[i[nu_mask] - M_old]
+    kr[nj_mask] = np.maximum(kr[nj_mask], kj_new[j[nj_mask] - N_old])
+    # users of increment k are [Mb[k-1], Mb[k]); items likewise
+    Mb = [M_old + int(np.searchsorted(ku, k, side="right")) for k in range(nk)]
+    Nb = [N_old + int(np.searchsorted(kj_new, k, side="right")) for k in range(nk)]
     t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
     old = kr < 0
     oi, oj, orr = t(i[old], torch.int32), t(j[old], torch.int32), t(r[old], torch.uint8)
@@ -361,23 +374,21 @@ def measure_serving(w, d, P, dev, frac=0.01, n_inc=4, rate=4000.0, horizon=2.0, 
     del col_ptr, row, rc
     incs = []
     prevM, prevN = M_old, N_old
-    for k in range(n_inc):
+    for k in range(nk):
         sel = kr == k
         incs.append((Mb[k] - prevM, Nb[k] - prevN, i[sel], j[sel], r[sel]))
         prevM, prevN = Mb[k], Nb[k]
-    rng = np.random.default_rng(seed)
     qt = poisson_times(rate, horizon, rng)
     qusers = [rng.integers(0, M_old, rng.integers(1, 17)).astype(np.int32) for _ in qt]
-    ut = [horizon * (k + 0.5) / n_inc for k in range(n_inc)]
+    ut = np.sort(rng.uniform(0.05, horizon, nk))
     events = sorted([(x, 0, q) for q, x in enumerate(qt)] + [(x, 1, k) for k, x in enumerate(ut)])
-    srv = Server(m, p, H, nbr, n=10, mode=1, max_users=4096)
+    srv = Server(m, p, H, nbr, n=10, mode=1, max_users=4096, depth=4)
     # warm-up: a few queries of each size class and nothing else
     for bs in (1, 16, 256):
         srv.submit_topn(rng.integers(0, M_old, bs).astype(np.int32))
-    while srv.step():
-        pass
+    srv.drain()
     torch.cuda.synchronize()
-    srv.calls, srv.users_served = {"topn": 0, "ingest": 0}, 0
+    srv.calls, srv.users_served, srv.max_inflight = {"topn": 0, "ingest": 0}, 0, 0
     qreq, ureq = [], []
 
     def produce():
@@ -392,19 +403,32 @@ def measure_serving(w, d, P, dev, frac=0.01, n_inc=4, rate=4000.0, horizon=2.0, 
                 ureq.append(srv.submit_ingest(*incs[idx]))
         srv.close()
 
+    import gc
+
     th = threading.Thread(target=produce)
+    gc.collect()          # the request backlog and the model's host state leave the collector's view first
+    gc.freeze()
     t0 = time.perf_counter()
     th.start()
-    srv.serve_forever()
+    srv.serve_forever(freeze_gc=False)
     th.join()
+    gc.unfreeze()
     wall = time.perf_counter() - t0
     m.check()
-    out = {"what": "serve.Server: Poisson top-N queries (1-16 users, mode 1, top-10) + online updates",
-           "rate_per_s": rate, "horizon_s": horizon, "updates": n_inc,
+    # queries answered while some update was running (submitted after its start, answered before its end)
+    spans = [(u.done - u.latency, u.done) for u in ureq if u.error is None]
+    during = sum(1 for q in qreq if q.error is None and any(a < q.arrival and q.done < b for a, b in spans))
+    out = {"what": "serve.Server: Poisson top-N queries (1-16 users, mode 1, top-10) + online updates of lognormal "
+                   "size, queries served from the last published model while updates run",
+           "rate_per_s": rate, "horizon_s": horizon, "updates": nk,
            "update_ratings": [int(len(x[2])) for x in incs],
-           "queries": latency_summary(qreq), "ingest": latency_summary(ureq),
-           "topn_calls": srv.calls["topn"], "mean_users_per_call": srv.users_served / max(1, srv.calls["topn"]),
+           "queries": latency_summary(qreq), "queries_split": split_summary(qreq), "ingest": latency_summary(ureq),
+           "queries_answered_during_an_update": int(during),
+           "topn_calls": srv.calls["topn"], "max_calls_in_flight": srv.max_inflight,
+           "mean_users_per_call": srv.users_served / max(1, srv.calls["topn"]),
            "users_per_s": srv.users_served / wall, "wall_s": round(wall, 3)}
+    for q in srv.qm:
+        q.close()
     m.close()
     return out
 

@@ -30,7 +30,13 @@
  *    LSHMF_ECUDA.  A failed call leaves outputs undefined.
  *  - Device memory the library needs beyond the caller's arrays is owned by
  *    the handle; a request that does not fit in free device memory returns
- *    LSHMF_ENOMEM before anything is launched.
+ *    LSHMF_ENOMEM before anything is launched.  These buffers come from one
+ *    stream-ordered memory pool per device that keeps freed memory for reuse
+ *    (lshmf_destroy hands unused pool memory back), and a handle reads its
+ *    small host results (counts, flags, sums) through its own page-locked
+ *    block: apart from lshmf_destroy, no call makes cudaFree or a pageable
+ *    copy, either of which would stall kernel launches of other host threads
+ *    (a query thread serving from another handle) until the device drains.
  *  - One handle must not be used from two host threads at once.
  *  - Ratings are small non-negative integers (uint8).  Signatures use the raw
  *    integer; training uses rating / rating_scale (Sec. 5.1 divides Yahoo!
@@ -281,6 +287,36 @@ lshmf_status lshmf_ingest(lshmf_handle *h, int64_t M_new, int64_t N_new, const i
  * Requires lshmf_prepare_training.  Asynchronous. */
 lshmf_status lshmf_topn(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n,
                         int32_t topn, int32_t mode, int32_t *d_items_out, float *d_scores_out, void *stream);
+
+/* lshmf_topn for callers that keep several top-N calls in flight (no
+ * counterpart in the paper: serving).  Same scores and order as lshmf_topn
+ * for the same users, mode and model, but nothing synchronises and the handle
+ * is only read: calls on one handle may run concurrently on different
+ * streams, issued from one host thread (not concurrently with a call that
+ * changes the handle: prepare, ingest, copy_serving into it).  Scratch is the
+ * caller's: d_work, at least lshmf_topn_work_bytes(h, n, mode) bytes,
+ * 16-byte aligned, one per call in flight.  A user id outside [0, M) gives
+ * its output row item -1 / score -infinity and records LSHMF_EINVAL in the
+ * handle's sticky flag (read by lshmf_check); EINVAL for bad arguments is
+ * returned before any launch.  Asynchronous. */
+lshmf_status lshmf_topn_async(lshmf_handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n,
+                              int32_t topn, int32_t mode, int32_t *d_items_out, float *d_scores_out,
+                              void *d_work, int64_t work_bytes, void *stream);
+
+/* Bytes of d_work lshmf_topn_async needs for n users in `mode` with the
+ * handle's current N (-1 on bad arguments). */
+int64_t lshmf_topn_work_bytes(const lshmf_handle *h, int64_t n, int32_t mode);
+
+/* Copies the serving state of src -- M, N, the per-user rating lists and the
+ * neighbour rows J^K -- into dst, so that lshmf_predict, lshmf_rmse and
+ * lshmf_topn(_async) on dst answer as on src (no counterpart in the paper:
+ * double-buffered serving while src takes online updates, Sec. 4.3).  The
+ * parameters stay the caller's arrays (pass the same lshmf_params to both).
+ * dst's blocked SGD layout is dropped (lshmf_train_epoch on dst returns
+ * ESTATE until a prepare).  F, K and rating_scale must match (EINVAL); ESTATE
+ * if src serves no model; ENOMEM before any copy if dst's buffers cannot
+ * grow.  Asynchronous on `stream` (src must not change until it completes). */
+lshmf_status lshmf_copy_serving(lshmf_handle *dst, const lshmf_handle *src, void *stream);
 
 /* Sizes of the prepared training layout (for memory planning and for the
  * algorithmic byte count of an epoch: every rating reads its user slot,

@@ -23,6 +23,10 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
                     const lshmf_params *p, int32_t epochs, cudaStream_t st);
 lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int32_t *qj, const uint8_t *qr,
                   int64_t n, double *h_rmse, cudaStream_t st);
+int64_t topn_work_bytes(const Handle *h, int64_t n, int32_t mode);
+lshmf_status topn_async(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_, int32_t mode,
+                        int32_t *d_items, float *d_scores, void *d_work, int64_t work_bytes, cudaStream_t st);
+lshmf_status copy_serving(Handle *dst, const Handle *src, cudaStream_t st);
 
 static lshmf_status validate_config(Handle *h, const lshmf_config *c) {
   if (!c) return set_err(h, LSHMF_EINVAL, "config is NULL");
@@ -73,10 +77,21 @@ lshmf_status lshmf_create(const lshmf_config *cfg, lshmf_handle **out) {
     delete hh;
     return LSHMF_ECUDA;
   }
+  if (cudaStreamCreateWithFlags(&h->alloc_st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete hh;
+    return LSHMF_ECUDA;
+  }
+  if (cudaHostAlloc(&h->h_stage, HOST_STAGE_BYTES, cudaHostAllocDefault) != cudaSuccess) {
+    cudaStreamDestroy(h->alloc_st);
+    delete hh;
+    return LSHMF_ENOMEM;
+  }
   if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMalloc(&h->d_red, 64) != cudaSuccess ||
       cudaMemset(h->d_err, 0, 64) != cudaSuccess) {
     cudaFree(h->d_err);
     cudaFree(h->d_red);
+    cudaStreamDestroy(h->alloc_st);
+    cudaFreeHost(h->h_stage);
     delete hh;
     return LSHMF_ENOMEM;
   }
@@ -88,19 +103,23 @@ void lshmf_destroy(lshmf_handle *hh) {
   if (!hh) return;
   Handle *h = &hh->h;
   cudaDeviceSynchronize();
-  for (auto &b : h->tmp) release(b);
-  for (auto &b : h->prep) release(b);
-  release(h->red_part);
-  release(h->aux);
-  release(h->lsh.sums);
-  for (auto &b : h->ing) release(b);
+  for (auto &b : h->tmp) release(h, b);
+  for (auto &b : h->prep) release(h, b);
+  release(h, h->red_part);
+  release(h, h->aux);
+  release(h, h->lsh.sums);
+  for (auto &b : h->ing) release(h, b);
   TrainLayout &t = h->tl;
   DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                     &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
-                          &t.seg_ck, &t.ck_roff, &t.df};
-  for (DevBuf *b : bufs) release(*b);
+                    &t.seg_ck, &t.ck_roff, &t.df, &t.sp_ptr, &t.sp_j, &t.sp_r};
+  for (DevBuf *b : bufs) release(h, *b);
+  cudaStreamSynchronize(h->alloc_st);
+  cudaStreamDestroy(h->alloc_st);
+  cudaFreeHost(h->h_stage);
   cudaFree(h->d_err);
   cudaFree(h->d_red);
+  trim_pool(h->device);   // memory no handle uses goes back to the device
   delete hh;
 }
 
@@ -232,6 +251,24 @@ lshmf_status lshmf_topn(lshmf_handle *hh, const lshmf_params *p, const int32_t *
   return topn(&hh->h, p, d_users, n, topn_, mode, d_items_out, d_scores_out, S(stream));
 }
 
+int64_t lshmf_topn_work_bytes(const lshmf_handle *hh, int64_t n, int32_t mode) {
+  if (!hh || n < 0 || (mode != 0 && mode != 1)) return -1;
+  return topn_work_bytes(&hh->h, n, mode);
+}
+
+lshmf_status lshmf_topn_async(lshmf_handle *hh, const lshmf_params *p, const int32_t *d_users, int64_t n,
+                              int32_t topn_, int32_t mode, int32_t *d_items_out, float *d_scores_out, void *d_work,
+                              int64_t work_bytes, void *stream) {
+  if (!hh) return LSHMF_EINVAL;
+  return topn_async(&hh->h, p, d_users, n, topn_, mode, d_items_out, d_scores_out, d_work, work_bytes, S(stream));
+}
+
+lshmf_status lshmf_copy_serving(lshmf_handle *dst, const lshmf_handle *src, void *stream) {
+  if (!dst || !src) return LSHMF_EINVAL;
+  if (dst == src) return set_err(&dst->h, LSHMF_EINVAL, "copy_serving: source and destination are the same handle");
+  return copy_serving(&dst->h, &src->h, S(stream));
+}
+
 lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out) {
   if (!hh || !out) return LSHMF_EINVAL;
   const Handle *h = &hh->h;
@@ -248,7 +285,7 @@ lshmf_status lshmf_training_stats(const lshmf_handle *hh, lshmf_train_stats *out
   for (const auto &b : h->prep) bytes += b.bytes;
   const DevBuf *bufs[] = {&t.sr, &t.rat, &t.mask, &t.roff, &t.packed, &t.seg_j, &t.seg_p0, &t.blk_seg, &t.blk_user,
                           &t.blk_order, &t.users, &t.nbr, &t.user_ptr, &t.csr_j, &t.csr_r, &t.bh0, &t.bh0n, &t.seg_sq,
-                          &t.seg_ck, &t.ck_roff, &t.df};
+                          &t.seg_ck, &t.ck_roff, &t.df, &t.sp_ptr, &t.sp_j, &t.sp_r};
   for (const DevBuf *b : bufs) bytes += b->bytes;
   for (const auto &b : h->ing) bytes += b.bytes;
   out->device_bytes = bytes + h->red_part.bytes + h->lsh.sums.bytes + h->aux.bytes;

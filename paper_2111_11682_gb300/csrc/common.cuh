@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <initializer_list>
 #include <cmath>
 #include <utility>
 #include <cstdarg>
@@ -23,7 +24,8 @@ extern std::atomic<int64_t> g_launches;
 // Device-side error flag values (bitwise OR of causes).
 enum : int32_t { DERR_INDEX = 1, DERR_DUP = 2, DERR_TIMEOUT = 4, DERR_CAPACITY = 8 };
 
-// Grow-only device buffer owned by a handle.
+// Grow-only device buffer owned by a handle, carved from the library's per-device
+// stream-ordered memory pool (see ensure()).
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -33,7 +35,22 @@ struct DevBuf {
 struct Handle;
 lshmf_status set_err(Handle *h, lshmf_status st, const char *fmt, ...);
 lshmf_status ensure(Handle *h, DevBuf &b, size_t bytes, const char *what);
-void release(DevBuf &b);
+void release(Handle *h, DevBuf &b);   // back to the pool; drops its bytes from the handle's account
+void trim_pool(int device);           // returns the pool's unused memory to the device
+
+// Small device-to-host reads (counts, flags, sums) go through the handle's
+// page-locked staging block: a copy into pageable memory holds a driver lock
+// until the stream reaches it, which stalls kernel launches from every other
+// host thread (a query thread of a server, say) for as long as the stream's
+// earlier kernels run.  read_back() copies each source into the staging block,
+// waits for the stream, then fills the destinations.
+struct HostRead {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+constexpr size_t HOST_STAGE_BYTES = 256;
+lshmf_status read_back(Handle *h, cudaStream_t st, std::initializer_list<HostRead> reads);
 
 // Training layout built by lshmf_prepare_training (all in blocked order).
 struct TrainLayout {
@@ -60,6 +77,7 @@ struct TrainLayout {
   DevBuf user_ptr;  // int64  [M + 1]: CSR of the training set by user (items ascending)
   DevBuf csr_j;     // int32  [nnz]
   DevBuf csr_r;     // uint8  [nnz]
+  DevBuf sp_ptr, sp_j, sp_r;   // spare per-user lists: an online update merges into them and swaps
   DevBuf bh0;       // float  [N]: bhat snapshot (per epoch)
   DevBuf bh0n;      // float  [N * K]: bhat snapshot of each item's neighbours
   DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
@@ -87,6 +105,8 @@ struct Handle {
   int num_sms = 0;
   int smem_optin = 0;   // opt-in shared memory per block (bytes)
   std::string last_error;
+  cudaStream_t alloc_st = nullptr;  // stream of the handle's pool allocations and frees
+  void *h_stage = nullptr;      // page-locked staging for read_back (HOST_STAGE_BYTES)
   int32_t *d_err = nullptr;     // device error flag (sticky until prepare)
   double *d_red = nullptr;      // small reduction output
   DevBuf tmp[8];                // scratch: [0..5] builders, [6] radix histogram, [7] scan

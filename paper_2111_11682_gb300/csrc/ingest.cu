@@ -487,7 +487,7 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   // per-user lists and the neighbour rows of the enlarged model, for prediction and top-N
   {
     const int64_t n_old = tl.nnz;
-    DevBuf np, nj, nr;
+    DevBuf &np = tl.sp_ptr, &nj = tl.sp_j, &nr = tl.sp_r;   // kept between updates (swapped with the lists)
     LSHMF_TRY(ensure(h, np, sizeof(int64_t) * (Mt + 1) * 2, "ingest merged user lists"));
     LSHMF_TRY(ensure(h, nj, sizeof(int32_t) * (n_old + n) + 64, "ingest merged user lists"));
     LSHMF_TRY(ensure(h, nr, size_t(n_old + n) + 64, "ingest merged user lists"));
@@ -502,15 +502,38 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
     std::swap(tl.user_ptr, np);
     std::swap(tl.csr_j, nj);
     std::swap(tl.csr_r, nr);
-    release(np);
-    release(nj);
-    release(nr);
     LSHMF_TRY(ensure(h, tl.nbr, sizeof(int32_t) * Nt * c.K, "layout neighbours"));
     LSHMF_CUDA(h, cudaMemcpyAsync(tl.nbr.p, d_nbr, sizeof(int32_t) * Nt * c.K, cudaMemcpyDeviceToDevice, st));
     tl.nnz = n_old + n;
     tl.serving = true;
   }
   return check_device_flag(h, st, "ingest");
+}
+
+// Serving state of src (sizes, per-user rating lists, neighbour rows) copied into dst, whose
+// prediction and top-N then answer as src does (the blocked SGD layout is not copied).
+lshmf_status copy_serving(Handle *dst, const Handle *src, cudaStream_t st) {
+  const TrainLayout &s = src->tl;
+  TrainLayout &d = dst->tl;
+  if (!s.serving) return set_err(dst, LSHMF_ESTATE, "copy_serving: the source serves no model yet");
+  if (dst->device != src->device) return set_err(dst, LSHMF_EINVAL, "copy_serving: handles on different devices");
+  if (dst->cfg.F != src->cfg.F || dst->cfg.K != src->cfg.K || dst->cfg.rating_scale != src->cfg.rating_scale)
+    return set_err(dst, LSHMF_EINVAL, "copy_serving: F, K and rating_scale must match");
+  const int64_t M = src->cfg.M, N = src->cfg.N, nnz = s.nnz;
+  LSHMF_TRY(ensure(dst, d.user_ptr, sizeof(int64_t) * (M + 1), "serving user lists"));
+  LSHMF_TRY(ensure(dst, d.csr_j, sizeof(int32_t) * nnz + 64, "serving user lists"));
+  LSHMF_TRY(ensure(dst, d.csr_r, size_t(nnz) + 64, "serving user lists"));
+  LSHMF_TRY(ensure(dst, d.nbr, sizeof(int32_t) * N * src->cfg.K, "serving neighbours"));
+  LSHMF_CUDA(dst, cudaMemcpyAsync(d.user_ptr.p, s.user_ptr.p, sizeof(int64_t) * (M + 1), cudaMemcpyDeviceToDevice, st));
+  LSHMF_CUDA(dst, cudaMemcpyAsync(d.csr_j.p, s.csr_j.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
+  LSHMF_CUDA(dst, cudaMemcpyAsync(d.csr_r.p, s.csr_r.p, size_t(nnz), cudaMemcpyDeviceToDevice, st));
+  LSHMF_CUDA(dst, cudaMemcpyAsync(d.nbr.p, s.nbr.p, sizeof(int32_t) * N * src->cfg.K, cudaMemcpyDeviceToDevice, st));
+  dst->cfg.M = M;
+  dst->cfg.N = N;
+  d.nnz = nnz;
+  d.ready = false;
+  d.serving = true;
+  return LSHMF_OK;
 }
 
 }  // namespace lshmf

@@ -984,7 +984,7 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   LSHMF_TRY(s);
   if (h_sq) {
     LSHMF_LAUNCH(h, k_sum_seg_sq, 1, 256, 0, st, tl.seg_sq.as<double>(), tl.nseg, h->d_red);
-    LSHMF_CUDA(h, cudaMemcpyAsync(h_sq, h->d_red, 8, cudaMemcpyDeviceToHost, st));
+    LSHMF_TRY(read_back(h, st, {{h_sq, h->d_red, 8}}));
     LSHMF_TRY(check_device_flag(h, st, "train"));
   }
   return LSHMF_OK;

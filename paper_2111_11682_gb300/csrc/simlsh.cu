@@ -674,10 +674,8 @@ lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *
   LSHMF_LAUNCH(h, k_sig_split_flags, g, 256, 0, st, unit_start, N, units);
   LSHMF_TRY(exclusive_scan_i64(h, units, split_idx, N, st));
   int64_t hb[2], nunits = 0, nsplit = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaMemcpyAsync(&nunits, unit_start + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaMemcpyAsync(&nsplit, split_idx + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{hb, bounds, sizeof(hb)}, {&nunits, unit_start + N, sizeof(int64_t)},
+                              {&nsplit, split_idx + N, sizeof(int64_t)}}));
   double psimax = 1.0;
   for (int q = 0; q < c.psi_pow; ++q) psimax *= double(hb[1]);
   const double bound = psimax * 2.0 * double(std::max<int64_t>(1, hb[0]));
@@ -746,14 +744,12 @@ lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *n
     LSHMF_TRY(radix_sort_pairs(h, k0, v0, k1, members, N, 64, st));
     LSHMF_LAUNCH(h, k_class_flags, gN, 256, 0, st, k1, members, sig, N, c.L, flag, h->d_err);
     int32_t herr = 0;
-    LSHMF_CUDA(h, cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st));
-    LSHMF_CUDA(h, cudaStreamSynchronize(st));
+    LSHMF_TRY(read_back(h, st, {{&herr, h->d_err, 4}}));
     if (!(herr & DERR_HASH)) break;
   }
   LSHMF_TRY(exclusive_scan_i64(h, flag, fscan, N, st));
   LSHMF_LAUNCH(h, k_class_emit, gN, 256, 0, st, flag, fscan, members, N, class_of, pos_of, cs);
-  LSHMF_CUDA(h, cudaMemcpyAsync(&ncls, fscan + N, 8, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&ncls, fscan + N, 8}}));
 
   // --- per-table buckets of classes: sort (t, key) -> class
   const int64_t n = int64_t(c.L) * ncls;
@@ -773,8 +769,7 @@ lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *n
   const unsigned gt = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ncls, TK_WARPS), 8L * h->num_sms));
   LSHMF_LAUNCH(h, k_topk_classes, gt, 32 * TK_WARPS, smem, st, a, ovf, ovf_ctr, ovf_ctr + 1);
   int32_t hovf[2] = {0, 0};
-  LSHMF_CUDA(h, cudaMemcpyAsync(hovf, ovf_ctr, 8, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{hovf, ovf_ctr, 8}}));
   if (hovf[0] > 0) {
     int logc = 1;
     while ((int64_t(1) << logc) < 2 * int64_t(hovf[1]) + 2) ++logc;

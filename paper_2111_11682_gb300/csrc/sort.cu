@@ -2,6 +2,9 @@
 // pairs and multi-level exclusive scans; plus the handle's buffer/status
 // utilities.  Used by the CSC/CSR/block layouts and by the per-table bucket
 // grouping of simLSH (Alg. 1).
+#include <cstring>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace lshmf {
@@ -20,44 +23,109 @@ lshmf_status set_err(Handle *h, lshmf_status st, const char *fmt, ...) {
   return st;
 }
 
+// Every grow-only buffer comes from one stream-ordered memory pool per device
+// that keeps freed memory mapped (release threshold: never).  A plain cudaFree
+// waits for the whole device while it blocks kernel launches from every other
+// host thread of the process; with the pool, a buffer that grows during an
+// online update (while another thread keeps answering queries) is returned and
+// re-taken without that stall, and usually without mapping new memory at all.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static lshmf_status device_pool(Handle *h, cudaMemPool_t *out) {
+  if (h->device < 0 || h->device >= 64) return set_err(h, LSHMF_ECUDA, "device %d outside the pool table", h->device);
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[h->device]) {
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = h->device;
+    cudaMemPool_t pool = nullptr;
+    LSHMF_CUDA(h, cudaMemPoolCreate(&pool, &pp));
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return set_err(h, LSHMF_ECUDA, "cudaMemPoolSetAttribute failed");
+    }
+    g_pool[h->device] = pool;
+  }
+  *out = g_pool[h->device];
+  return LSHMF_OK;
+}
+
+void trim_pool(int device) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (device >= 0 && device < 64 && g_pool[device]) cudaMemPoolTrimTo(g_pool[device], 0);
+}
+
 lshmf_status ensure(Handle *h, DevBuf &b, size_t bytes, const char *what) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return LSHMF_OK;
   if (h->mem_limit > 0 && h->held - int64_t(b.bytes) + int64_t(bytes) > h->mem_limit)
     return set_err(h, LSHMF_ENOMEM, "%s: %zu bytes requested, the handle's memory limit is %lld (holds %lld)", what,
                    bytes, (long long)h->mem_limit, (long long)h->held);
+  // a buffer that grows again (online updates enlarge the model a little at a time) takes 25 % headroom,
+  // so that it is replaced rarely
   if (b.p) {
-    cudaDeviceSynchronize();   // in-flight kernels may still use the old block
-    cudaFree(b.p);
+    const size_t roomy = std::max(bytes, b.bytes + b.bytes / 4);
+    if (h->mem_limit <= 0 || h->held - int64_t(b.bytes) + int64_t(roomy) <= h->mem_limit) bytes = roomy;
+  }
+  cudaMemPool_t pool = nullptr;
+  LSHMF_TRY(device_pool(h, &pool));
+  if (b.p) {
+    LSHMF_CUDA(h, cudaDeviceSynchronize());   // in-flight kernels may still use the old block
+    LSHMF_CUDA(h, cudaFreeAsync(b.p, h->alloc_st));
     h->held -= int64_t(b.bytes);
     b.p = nullptr;
     b.bytes = 0;
   }
   size_t free_b = 0, total_b = 0;
   LSHMF_CUDA(h, cudaMemGetInfo(&free_b, &total_b));
+  uint64_t reserved = 0, used = 0;   // memory the pool holds mapped but has not handed out counts as free
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  const size_t avail = free_b + size_t(reserved > used ? reserved - used : 0);
   const size_t margin = size_t(256) << 20;
-  if (bytes + margin > free_b)
-    return set_err(h, LSHMF_ENOMEM, "%s: %zu bytes requested, %zu free", what, bytes, free_b);
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (bytes + margin > avail)
+    return set_err(h, LSHMF_ENOMEM, "%s: %zu bytes requested, %zu free", what, bytes, avail);
+  cudaError_t e = cudaMallocFromPoolAsync(&b.p, bytes, pool, h->alloc_st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->alloc_st);   // usable from any stream once this returns
   if (e != cudaSuccess) {
+    if (b.p) cudaFreeAsync(b.p, h->alloc_st);
     b.p = nullptr;
-    return set_err(h, LSHMF_ENOMEM, "%s: cudaMalloc(%zu): %s", what, bytes, cudaGetErrorString(e));
+    return set_err(h, LSHMF_ENOMEM, "%s: pool allocation of %zu bytes: %s", what, bytes, cudaGetErrorString(e));
   }
   b.bytes = bytes;
   h->held += int64_t(bytes);
   return LSHMF_OK;
 }
 
-void release(DevBuf &b) {
-  if (b.p) cudaFree(b.p);
+void release(Handle *h, DevBuf &b) {
+  if (b.p) cudaFreeAsync(b.p, h->alloc_st);
+  h->held -= int64_t(b.bytes);
   b.p = nullptr;
   b.bytes = 0;
 }
 
+lshmf_status read_back(Handle *h, cudaStream_t st, std::initializer_list<HostRead> reads) {
+  size_t off = 0;
+  for (const HostRead &r : reads) {
+    if (off + r.bytes > HOST_STAGE_BYTES) return set_err(h, LSHMF_EINVAL, "read_back: %zu bytes exceed the staging block", off + r.bytes);
+    LSHMF_CUDA(h, cudaMemcpyAsync(static_cast<char *>(h->h_stage) + off, r.src, r.bytes, cudaMemcpyDeviceToHost, st));
+    off += (r.bytes + 7) & ~size_t(7);
+  }
+  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  off = 0;
+  for (const HostRead &r : reads) {
+    memcpy(r.dst, static_cast<const char *>(h->h_stage) + off, r.bytes);
+    off += (r.bytes + 7) & ~size_t(7);
+  }
+  return LSHMF_OK;
+}
+
 lshmf_status check_device_flag(Handle *h, cudaStream_t st, const char *what) {
   int32_t flag = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&flag, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&flag, h->d_err, sizeof(int32_t)}}));
   if (flag == 0) return LSHMF_OK;
   if (flag & DERR_TIMEOUT)
     return set_err(h, LSHMF_ETIMEOUT, "%s: a bounded device wait gave up (flag %d)", what, flag);

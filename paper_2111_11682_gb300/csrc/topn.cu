@@ -455,20 +455,39 @@ k_tc_rerank(const TopnArgs a, const int32_t *users, int64_t nq, const int32_t *c
   }
 }
 
-lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_, int32_t mode,
-                  int32_t *d_items, float *d_scores, cudaStream_t st) {
+// Checks a top-N call's arguments (EINVAL); shared by the synchronous and the asynchronous entry point.
+static lshmf_status topn_check(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_,
+                               int32_t mode, int32_t *d_items, float *d_scores) {
   const lshmf_config &c = h->cfg;
-  const TrainLayout &tl = h->tl;
-  if (!tl.serving) return set_err(h, LSHMF_ESTATE, "topn: lshmf_prepare_training has not succeeded");
+  if (!h->tl.serving) return set_err(h, LSHMF_ESTATE, "topn: lshmf_prepare_training has not succeeded");
   if (mode != 0 && mode != 1)
     return set_err(h, LSHMF_EINVAL, "topn: mode %d is not available (0 = FP32, 1 = BF16 candidates + FP32 rerank)", mode);
   if (c.N > TOPN_MAX_N) return set_err(h, LSHMF_EINVAL, "topn: N = %lld above %lld", (long long)c.N, (long long)TOPN_MAX_N);
   if (topn_ < 1 || topn_ > 1024) return set_err(h, LSHMF_EINVAL, "topn: topn must be in [1, 1024]");
   if (n < 0) return set_err(h, LSHMF_EINVAL, "topn: n < 0");
-  if (n == 0) return LSHMF_OK;
-  if (!d_users || !d_items || !d_scores) return set_err(h, LSHMF_EINVAL, "topn: null pointer");
+  if (n > 0 && (!d_users || !d_items || !d_scores)) return set_err(h, LSHMF_EINVAL, "topn: null pointer");
   if (!p || !p->U || !p->V || !p->b || !p->bh || !p->W || !p->C) return set_err(h, LSHMF_EINVAL, "topn: null parameter");
-  LSHMF_TRY(check_range_i32(h, d_users, n, c.M, st, "topn (users)"));
+  if (mode == 1 && c.F > TC_FMAX) return set_err(h, LSHMF_EINVAL, "topn: mode 1 needs F <= %d", TC_FMAX);
+  if (mode == 1 && topn_ > TC_C) return set_err(h, LSHMF_EINVAL, "topn: mode 1 needs topn <= %d", TC_C);
+  return LSHMF_OK;
+}
+
+// Candidate slots per user of mode 1 (a function of N only).
+static int topn_ncand(const Handle *h, int *nslices_out, int *tps_out) {
+  const int tiles = int((h->cfg.N + TC_N - 1) / TC_N);
+  int nslices = int(std::min<int64_t>(TC_MAX_SLICES, tiles));
+  const int tps = (tiles + nslices - 1) / nslices;
+  nslices = (tiles + tps - 1) / tps;
+  if (nslices_out) *nslices_out = nslices;
+  if (tps_out) *tps_out = tps;
+  return nslices * TC_C;
+}
+
+// The kernels of one top-N call on users d_users (all in [0, M)); cand: n * ncand ints (mode 1).
+static lshmf_status topn_launch(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_,
+                                int32_t mode, int32_t *d_items, float *d_scores, int32_t *cand, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  const TrainLayout &tl = h->tl;
   TopnArgs a;
   a.user_ptr = tl.user_ptr.as<int64_t>();
   a.csr_j = tl.csr_j.as<int32_t>();
@@ -482,8 +501,6 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
   a.K = c.K;
   a.topn = topn_;
   if (mode == 1) {
-    if (c.F > TC_FMAX) return set_err(h, LSHMF_EINVAL, "topn: mode 1 needs F <= %d", TC_FMAX);
-    if (topn_ > TC_C) return set_err(h, LSHMF_EINVAL, "topn: mode 1 needs topn <= %d", TC_C);
     TcArgs t;
     t.U = p->U; t.V = p->V; t.bh = p->bh;
     t.user_ptr = a.user_ptr;
@@ -497,12 +514,8 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
     const int64_t utiles = (n + TC_M - 1) / TC_M;
     // item slices: a function of N only, so that a user's candidates (and result) do not depend on the
     // other users of the batch
-    t.nslices = int(std::min<int64_t>(TC_MAX_SLICES, t.tiles));
-    t.tiles_per_slice = (t.tiles + t.nslices - 1) / t.nslices;
-    t.nslices = (t.tiles + t.tiles_per_slice - 1) / t.tiles_per_slice;
-    const int ncand = t.nslices * TC_C;
-    LSHMF_TRY(ensure(h, h->ing[6], sizeof(int32_t) * size_t(n) * ncand + 64, "topn candidates"));
-    t.cand = h->ing[6].as<int32_t>();
+    const int ncand = topn_ncand(h, &t.nslices, &t.tiles_per_slice);
+    t.cand = cand;
     t.err = h->d_err;
     // shared memory: the two BF16 tiles, at least 100 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
     const size_t tsmem = std::max<size_t>(size_t(TC_M + TC_N) * t.Fp * 2 + 1024, size_t(100) * 1024);
@@ -512,7 +525,7 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
     const size_t rsmem = sizeof(uint16_t) * size_t(c.N) + 16;
     LSHMF_CUDA(h, cudaFuncSetAttribute(k_tc_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
     const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n, 4L * h->num_sms));
-    LSHMF_LAUNCH(h, k_tc_rerank, gr, RR_THREADS, rsmem, st, a, d_users, n, t.cand, ncand, d_items, d_scores);
+    LSHMF_LAUNCH(h, k_tc_rerank, gr, RR_THREADS, rsmem, st, a, d_users, n, cand, ncand, d_items, d_scores);
     return LSHMF_OK;
   }
   const size_t smem = sizeof(float) * c.N + sizeof(float) * ((c.F + 3) & ~3) + sizeof(uint16_t) * c.N + 16;
@@ -520,6 +533,69 @@ lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int6
   LSHMF_CUDA(h, cudaFuncSetAttribute(k_topn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)std::min<int64_t>(n, 8L * h->num_sms);
   LSHMF_LAUNCH(h, k_topn_f32, grid, TOPN_THREADS, smem, st, a, d_users, n, d_items, d_scores);
+  return LSHMF_OK;
+}
+
+lshmf_status topn(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_, int32_t mode,
+                  int32_t *d_items, float *d_scores, cudaStream_t st) {
+  LSHMF_TRY(topn_check(h, p, d_users, n, topn_, mode, d_items, d_scores));
+  if (n == 0) return LSHMF_OK;
+  LSHMF_TRY(check_range_i32(h, d_users, n, h->cfg.M, st, "topn (users)"));
+  int32_t *cand = nullptr;
+  if (mode == 1) {
+    const int ncand = topn_ncand(h, nullptr, nullptr);
+    LSHMF_TRY(ensure(h, h->ing[6], sizeof(int32_t) * size_t(n) * ncand + 64, "topn candidates"));
+    cand = h->ing[6].as<int32_t>();
+  }
+  return topn_launch(h, p, d_users, n, topn_, mode, d_items, d_scores, cand, st);
+}
+
+// ---------------------------------------------------------- asynchronous ----
+// Users of an asynchronous call: out-of-range ids are replaced by 0 (so the kernels read valid rows),
+// marked invalid, and recorded in the handle's sticky error flag.
+__global__ void k_topn_users(const int32_t *users, int64_t n, int64_t M, int32_t *safe, int32_t *valid, int32_t *err) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t u = users[q];
+    const bool ok = u >= 0 && u < M;
+    safe[q] = ok ? u : 0;
+    valid[q] = ok ? 1 : 0;
+    if (!ok) atomicOr(err, DERR_INDEX);
+  }
+}
+
+// Rows of invalid users: item -1, score -infinity.
+__global__ void k_topn_fix(const int32_t *valid, int64_t n, int topn, int32_t *items, float *scores) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n * topn; x += int64_t(gridDim.x) * blockDim.x)
+    if (!valid[x / topn]) {
+      items[x] = -1;
+      scores[x] = -INFINITY;
+    }
+}
+
+int64_t topn_work_bytes(const Handle *h, int64_t n, int32_t mode) {
+  if (n < 0) return -1;
+  const int64_t users = 2 * n * int64_t(sizeof(int32_t));
+  const int64_t cand = mode == 1 ? n * int64_t(topn_ncand(h, nullptr, nullptr)) * int64_t(sizeof(int32_t)) : 0;
+  return users + cand + 256;
+}
+
+lshmf_status topn_async(Handle *h, const lshmf_params *p, const int32_t *d_users, int64_t n, int32_t topn_, int32_t mode,
+                        int32_t *d_items, float *d_scores, void *d_work, int64_t work_bytes, cudaStream_t st) {
+  LSHMF_TRY(topn_check(h, p, d_users, n, topn_, mode, d_items, d_scores));
+  if (n == 0) return LSHMF_OK;
+  if (!d_work) return set_err(h, LSHMF_EINVAL, "topn_async: null workspace");
+  if (reinterpret_cast<uintptr_t>(d_work) % 16 != 0) return set_err(h, LSHMF_EINVAL, "topn_async: workspace not 16-byte aligned");
+  const int64_t need = topn_work_bytes(h, n, mode);
+  if (work_bytes < need)
+    return set_err(h, LSHMF_EINVAL, "topn_async: workspace of %lld bytes, %lld needed", (long long)work_bytes,
+                   (long long)need);
+  int32_t *safe = static_cast<int32_t *>(d_work), *valid = safe + n;
+  int32_t *cand = reinterpret_cast<int32_t *>(reinterpret_cast<uintptr_t>(valid + n + 63) & ~uintptr_t(255));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4L * h->num_sms));
+  LSHMF_LAUNCH(h, k_topn_users, g, 256, 0, st, d_users, n, h->cfg.M, safe, valid, h->d_err);
+  LSHMF_TRY(topn_launch(h, p, safe, n, topn_, mode, d_items, d_scores, cand, st));
+  const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n * topn_, 256), 4L * h->num_sms));
+  LSHMF_LAUNCH(h, k_topn_fix, gf, 256, 0, st, valid, n, topn_, d_items, d_scores);
   return LSHMF_OK;
 }
 

@@ -378,8 +378,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   LSHMF_LAUNCH(h, k_emit_A, g, 256, 0, st, k1, v1, d_r, nnz, ibits, iA, jA, rA, red, h->d_err);
   LSHMF_TRY(check_device_flag(h, st, "prepare_training"));
   unsigned long long hsum = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&hsum, red, sizeof(hsum), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&hsum, red, sizeof(hsum)}}));
   const double mu = double(hsum) / double(nnz) / double(c.rating_scale);
 
   // persistent layout buffers
@@ -404,8 +403,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   // item runs ("segments") inside blocks
   LSHMF_TRY(exclusive_scan_i64(h, fl, fs, nnz, st));
   int64_t nseg = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&nseg, fs + nnz, 8, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&nseg, fs + nnz, 8}}));
   tl.nseg = nseg;
   LSHMF_TRY(ensure(h, tl.seg_j, nseg * 4, "layout segment items"));
   LSHMF_TRY(ensure(h, tl.seg_p0, (nseg + 1) * 8, "layout segment starts"));
@@ -424,8 +422,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   LSHMF_LAUNCH(h, k_run_flags, g, 256, 0, st, kU, nnz, fl);
   LSHMF_TRY(exclusive_scan_i64(h, fl, rscan, nnz, st));
   int64_t nruns = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&nruns, rscan + nnz, 8, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&nruns, rscan + nnz, 8}}));
   LSHMF_TRY(ensure(h, tl.users, nruns * 4, "layout users"));
   LSHMF_LAUNCH(h, k_runs, g, 256, 0, st, kU, rscan, fl, nnz, ibits, tl.users.as<int32_t>(), run_pos, run_blk);
   LSHMF_LAUNCH(h, k_group_ptr, grid_for(h, nruns + 1), 256, 0, st, run_blk, 0, nruns, NB,
@@ -457,9 +454,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
   LSHMF_TRY(exclusive_scan_i64(h, cnt, roff, nnz, st));
   int64_t npacked = 0;
   unsigned long long hred[4] = {0, 0, 0, 0};
-  LSHMF_CUDA(h, cudaMemcpyAsync(&npacked, roff + nnz, 8, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaMemcpyAsync(hred, red, 32, cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&npacked, roff + nnz, 8}, {hred, red, 32}}));
   tl.npacked = npacked;
   LSHMF_TRY(ensure(h, tl.packed, npacked + 64, "layout packed neighbour ratings"));
   if (wide) {
@@ -481,8 +476,7 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
     LSHMF_LAUNCH(h, k_seg_nck, grid_for(h, nseg), 256, 0, st, tl.seg_p0.as<int64_t>(), nseg, nck);
     LSHMF_TRY(exclusive_scan_i64(h, nck, ckscan, nseg, st));
     int64_t nchunks = 0;
-    LSHMF_CUDA(h, cudaMemcpyAsync(&nchunks, ckscan + nseg, 8, cudaMemcpyDeviceToHost, st));
-    LSHMF_CUDA(h, cudaStreamSynchronize(st));
+    LSHMF_TRY(read_back(h, st, {{&nchunks, ckscan + nseg, 8}}));
     tl.nchunks = nchunks;
     LSHMF_TRY(ensure(h, tl.seg_ck, (nseg + 1) * 4, "layout run chunks"));
     LSHMF_TRY(ensure(h, tl.ck_roff, nchunks * 8 + 8, "layout chunk offsets"));
@@ -649,7 +643,7 @@ lshmf_status rmse(Handle *h, const lshmf_params *p, const int32_t *qi, const int
   LSHMF_LAUNCH(h, k_sqerr, RMSE_CTAS, 256, 0, st, pred_args(h, p), qi, qj, qr, n, part);
   LSHMF_LAUNCH(h, k_sum_f64, 1, 256, 0, st, part, (int64_t)RMSE_CTAS, h->d_red);
   double s = 0.0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&s, h->d_red, 8, cudaMemcpyDeviceToHost, st));
+  LSHMF_TRY(read_back(h, st, {{&s, h->d_red, 8}}));
   LSHMF_TRY(check_device_flag(h, st, "rmse"));
   *h_rmse = double(h->cfg.rating_scale) * std::sqrt(s / double(n));
   return LSHMF_OK;
@@ -669,7 +663,7 @@ lshmf_status rmse_with_scratch(Handle *h, const lshmf_params *p, const int32_t *
   LSHMF_LAUNCH(h, k_sqerr, (unsigned)ctas, 256, 0, st, pred_args(h, p), qi, qj, qr, n, scratch);
   LSHMF_LAUNCH(h, k_sum_f64, 1, 256, 0, st, scratch, ctas, scratch + ctas);
   double s = 0.0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&s, scratch + ctas, 8, cudaMemcpyDeviceToHost, st));
+  LSHMF_TRY(read_back(h, st, {{&s, scratch + ctas, 8}}));
   LSHMF_TRY(check_device_flag(h, st, "rmse"));
   *h_rmse = double(h->cfg.rating_scale) * std::sqrt(s / double(n));
   return LSHMF_OK;

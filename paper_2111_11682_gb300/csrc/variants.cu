@@ -179,8 +179,7 @@ lshmf_status build_neighbours_variant(Handle *h, int32_t gen, const int64_t *col
   LSHMF_LAUNCH(h, k_units, g, 256, 0, st, col_ptr, N, units);
   LSHMF_TRY(exclusive_scan_i64(h, units, unit_start, N, st));
   int64_t nunits = 0;
-  LSHMF_CUDA(h, cudaMemcpyAsync(&nunits, unit_start + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  LSHMF_CUDA(h, cudaStreamSynchronize(st));
+  LSHMF_TRY(read_back(h, st, {{&nunits, unit_start + N, sizeof(int64_t)}}));
   LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * N + 16, "signatures"));
   uint32_t *sig = h->tmp[0].as<uint32_t>();
   const unsigned gu = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nunits, 16L * h->num_sms));

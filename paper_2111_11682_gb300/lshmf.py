@@ -21,7 +21,8 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "lshmf_launch_count", "lshmf_set_option",
            "lshmf_csc_from_coo", "lshmf_build_neighbours", "lshmf_signatures", "lshmf_prepare_training", "lshmf_train_epoch",
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
-           "lshmf_ingest", "lshmf_topn", "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant",
+           "lshmf_ingest", "lshmf_topn", "lshmf_topn_async", "lshmf_topn_work_bytes", "lshmf_copy_serving",
+           "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant",
            "lshmf_batch_create", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
 
 GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
@@ -106,6 +107,9 @@ def load(build_if_missing: bool = True):
         "lshmf_rmse_noalloc": ([P, CP, P, P, P, I64, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lshmf_ingest": ([P, I64, I64, P, P, P, I64, P, P, P, CP, I32, P], ctypes.c_int),
         "lshmf_topn": ([P, CP, P, I64, I32, I32, P, P, P], ctypes.c_int),
+        "lshmf_topn_async": ([P, CP, P, I64, I32, I32, P, P, P, I64, P], ctypes.c_int),
+        "lshmf_topn_work_bytes": ([P, I64, I32], I64),
+        "lshmf_copy_serving": ([P, P, P], ctypes.c_int),
         "lshmf_batch_create": ([P, CP, P, I32, I32, I32, I32, ctypes.POINTER(P)], ctypes.c_int),
         "lshmf_batch_plan": ([P, I32, I32, P, P], ctypes.c_int),
         "lshmf_batch_run": ([P, P], ctypes.c_int),
@@ -309,6 +313,22 @@ class LshMF:
         self._chk(self.lib.lshmf_topn(self.h, ctypes.byref(cp), _ptr(users), q, n, mode, _ptr(items), _ptr(scores),
                                       _stream(stream)))
         return items, scores
+
+    def topn_work_bytes(self, n: int, mode: int = 0) -> int:
+        """lshmf_topn_work_bytes: workspace bytes of lshmf_topn_async for n users."""
+        return int(self.lib.lshmf_topn_work_bytes(self.h, n, mode))
+
+    def topn_async(self, p: Params, users, n: int, mode: int, work, items, scores, stream=None):
+        """lshmf_topn_async: enqueues top-n of `users` into items [q x n] / scores [q x n] with the caller's
+        workspace `work` (a CUDA uint8 tensor of at least topn_work_bytes(q, mode) bytes); nothing waits."""
+        cp = p._c()
+        self._chk(self.lib.lshmf_topn_async(self.h, ctypes.byref(cp), _ptr(users), users.numel(), n, mode,
+                                            _ptr(items), _ptr(scores), _ptr(work), work.numel(), _stream(stream)))
+
+    def copy_serving(self, src: "LshMF", stream=None):
+        """lshmf_copy_serving: this handle now serves src's model (sizes, per-user lists, neighbour rows)."""
+        self._chk(self.lib.lshmf_copy_serving(self.h, src.h, _stream(stream)))
+        self.cfg.M, self.cfg.N = src.cfg.M, src.cfg.N
 
     def rmse_noalloc(self, p: Params, users, items, r, stream=None) -> float:
         """lshmf_rmse_noalloc: same result as rmse() without any device allocation."""
