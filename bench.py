@@ -479,30 +479,33 @@ def measure_generators(w, d, P, dev, reps=3):
 
 
 def measure_batch(dev, n_inst=256, E=3, seed=7):
-    """Many small independent models trained together: `n_inst` uneven instances (users 1k-40k and
-    items 300-4k log-uniform, density 0.5-3 %, at most 600k ratings; F = K = 32, L = 8, bits = 8),
-    simLSH neighbours, P of each chosen by the autotuner (least SM-time per epoch among 4..64, the
-    fastest P for instances that would otherwise be the batch's critical path).
+    """Many independent models trained together, shaped like the batched multi-instance workload:
+    `n_inst` instances whose size follows one log-uniform draw s in [0, 1] each -- users 1k x 50^s,
+    items 500 x 40^s, ratings 10k x 500^s (1k x 500 with 10k ratings up to 50k x 20k with 5M) --
+    integer ratings 1-5 with Zipf items, F = 32, K = 16, simLSH neighbours (L = 8 tables x 8 bits),
+    Eq. (7) with beta = 0.3.  The autotuner picks each instance's P (least SM-time per epoch among
+    4..64; the fastest P for instances that would otherwise be the batch's critical path) and the
+    SGD kernel's tile (groups per CTA, blocks in flight).
     Times E epochs of every instance (CUDA events around the whole job, parameters reset untimed):
-    per-instance lshmf_train_epoch calls from a host loop, against one CUDA graph of the whole job
-    (lshmf_batch) with instances on 1 or more parallel branches, round-robin or longest-first by the
-    autotuner's epoch time."""
+    per-instance lshmf_train_epoch calls from a host loop (one run), against one CUDA graph of the
+    whole job (lshmf_batch) with instances on parallel branches, round-robin or longest-first by the
+    autotuner's epoch time (median of 3 after one warm-up).  sm_time_bound_ms = E x the sum over
+    instances of epoch ms x min(P, SMs) / SMs, the least time the SMs allow."""
     import dataclasses
 
     import torch
 
     import synth
-    from paper_2111_11682_gb300 import (Batch, Config, LshMF, Params, autotune_P, config_from_workload,
-                                        plan_batch_P)
+    from paper_2111_11682_gb300 import (OPT_SGD_GROUPS, OPT_SGD_SLOTS, Batch, Config, LshMF, Params, autotune_P,
+                                        autotune_tile, config_from_workload, plan_batch_P)
 
     rng = np.random.default_rng(seed)
     t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
-    models, inits, nnz_all, timings, data, t0 = [], [], [], [], [], time.time()
+    models, inits, nnz_all, timings, data, tiles, t0 = [], [], [], [], [], [], time.time()
     for x in range(n_inst):
-        M = int(np.exp(rng.uniform(np.log(1000), np.log(40000))))
-        N = int(np.exp(rng.uniform(np.log(300), np.log(4000))))
-        nnz = int(min(600_000, max(2000, M * N * rng.uniform(0.005, 0.03))))
-        w = dataclasses.replace(synth.TINY, name=f"inst{x}", M=M, N=N, nnz=nnz, F=32, K=32, L=8, bits=8,
+        sz = rng.uniform(0.0, 1.0)
+        M, N, nnz = int(round(1000 * 50 ** sz)), int(round(500 * 40 ** sz)), int(round(10_000 * 500 ** sz))
+        w = dataclasses.replace(synth.TINY, name=f"inst{x}", M=M, N=N, nnz=nnz, F=32, K=16, L=8, bits=8,
                                 beta=0.3, seed=1000 + x, test_frac=0.0)
         d = synth.generate(w)
         m0 = LshMF(config_from_workload(w))
@@ -510,9 +513,11 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
         col_ptr, row, rc = m0.csc_from_coo(ti, tj, tr)
         nbr = m0.build_neighbours(col_ptr, row, rc, t(d["H"].view(np.int64), torch.int64))
         p0 = Params.from_init(d["U0"], d["V0"], w.K, dev)
-        m, mu, tim = autotune_P(m0.cfg, ti, tj, tr, nbr, p0, candidates=(4, 8, 16, 32, 64), reps=1)
+        m, mu, tim = autotune_P(m0.cfg, ti, tj, tr, nbr, p0, candidates=(4, 8, 16), reps=1)
         m0.close()
         p0.mu = mu
+        tile, _ = autotune_tile(m, p0, tiles=((3, 0), (2, 0), (1, 0)), reps=1)
+        tiles.append(tile)
         timings.append(tim)
         data.append((ti, tj, tr, nbr))
         models.append(m)
@@ -528,6 +533,8 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
             m = LshMF(Config.make(c.M, c.N, c.F, c.K, c.L, c.bits, c.psi_pow, P, list(c.alpha), c.beta,
                                   list(c.lambda_), c.rating_scale))
             m.prepare_training(*data[x])
+            m.set_option(OPT_SGD_GROUPS, tiles[x][0])
+            m.set_option(OPT_SGD_SLOTS, tiles[x][1])
             models[x].close()
             models[x] = m
             moved += 1
@@ -564,13 +571,15 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
            "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
            "instances": n_inst, "ratings": int(sum(nnz_all)), "epochs": E,
            "P_histogram": {str(k): int(v) for k, v in zip(*np.unique([m.cfg.P for m in models], return_counts=True))},
+           "tile_histogram (groups, slots; 0 = as many as fit)": {
+               str(k): int(v) for k, v in zip(*np.unique(["%d,%d" % t for t in tiles], return_counts=True))},
            "moved_to_fastest_P": moved, "setup_s": round(setup_s, 1), "modes": {}}
-    timed(eager, reps=1)
-    ms = timed(eager)
+    out["sm_time_bound_ms"] = round(E * sum(c * min(m.cfg.P, sms) for c, m in zip(costs, models)) / sms, 2)
+    ms = timed(eager, reps=1)      # the autotuner already ran every model's kernels
     out["modes"]["per_instance_calls"] = {"ms": round(ms, 2), "rating_updates_per_s": total / (ms / 1e3)}
     ref = [q.clone() for q in ps]
     fill = int(math.ceil(sms / np.mean([min(m.cfg.P, sms) for m in models])))   # branches that fill the SMs
-    for nb, cost in ((1, None), (32, None), (fill, costs), (2 * fill, costs)):
+    for nb, cost in ((32, None), (fill, costs), (2 * fill, costs)):
         b = Batch(models, ps, epoch0=0, epochs=E, branches=nb, cost=cost)
         timed(b.run, reps=1)
         ms = timed(b.run)
@@ -620,7 +629,9 @@ def sgd_roofline(stats, w, epoch_ms, P):
     prof = profile_entry("sgd_epoch", w.name, kernel_hash())
     return {"bound": "hbm", "kernel": "SGD epoch kernel", "achieved": round(achieved, 1),
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+            "traffic": prof.get("dram_bytes_per_epoch") if prof else None,
+            "traffic_per_launch": prof.get("dram_bytes_per_launch") if prof else None,
+            "traffic_note": "ncu DRAM bytes per epoch (P launches), like achieved; from profiles/dram_traffic.json",
             "algorithmic_bytes_per_epoch": int(bytes_ep),
             "min_bytes_per_epoch": int(sgd_min_bytes_per_epoch(stats, w)),
             "min_bytes_achieved_gbs": round(sgd_min_bytes_per_epoch(stats, w) / (ep_med / 1e3) / 1e9, 1),

@@ -121,6 +121,9 @@ int64_t lshmf_launch_count(void);
  *  LSHMF_OPT_SGD_SLOTS     blocks of the schedule held at once by one CTA of the
  *      SGD kernel (0 = as many as fit in shared memory, at most 4).  The result
  *      does not depend on it.
+ *  LSHMF_OPT_SGD_GROUPS    consumer/producer groups (one consumer and four
+ *      producer warps each) per CTA of the SGD kernel (0 = as many as fit in
+ *      shared memory, at most 3).  The result does not depend on it.
  *  LSHMF_OPT_TEST_WITHHOLD test hook, 1 = the SGD kernel never tells the first
  *      pipeline of each CTA that the stratum's work is all handed out, so its
  *      producers wait for a flag that nothing sets until their poll limit runs
@@ -130,6 +133,7 @@ int64_t lshmf_launch_count(void);
 #define LSHMF_OPT_WAIT_POLLS 2
 #define LSHMF_OPT_SGD_SLOTS 3
 #define LSHMF_OPT_TEST_WITHHOLD 4
+#define LSHMF_OPT_SGD_GROUPS 5
 lshmf_status lshmf_set_option(lshmf_handle *h, int32_t option, int64_t value);
 
 /* Item-major (CSC) layout of a rating set: Sec. 4.1 computes each item's hash

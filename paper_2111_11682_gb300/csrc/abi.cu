@@ -145,8 +145,12 @@ lshmf_status lshmf_set_option(lshmf_handle *hh, int32_t option, int64_t value) {
       h->wait_polls = value;
       return LSHMF_OK;
     case LSHMF_OPT_SGD_SLOTS:
-      if (value < 0 || value > 4) return set_err(h, LSHMF_EINVAL, "set_option: SGD block slots in [0, 4]");
+      if (value < 0 || value > SGD_MAX_SLOTS) return set_err(h, LSHMF_EINVAL, "set_option: SGD block slots in [0, %d]", SGD_MAX_SLOTS);
       h->sgd_slots = int32_t(value);
+      return LSHMF_OK;
+    case LSHMF_OPT_SGD_GROUPS:
+      if (value < 0 || value > SGD_MAX_GROUPS) return set_err(h, LSHMF_EINVAL, "set_option: SGD groups in [0, %d]", SGD_MAX_GROUPS);
+      h->sgd_groups = int32_t(value);
       return LSHMF_OK;
     case LSHMF_OPT_TEST_WITHHOLD:
       if (value < 0 || value > 1) return set_err(h, LSHMF_EINVAL, "set_option: test hook is 0 or 1");

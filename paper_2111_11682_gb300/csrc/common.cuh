@@ -121,6 +121,7 @@ struct Handle {
   int64_t held = 0;             // bytes held in grow-only buffers (ensure)
   int64_t wait_polls = 0;       // polls before a device-side wait gives up (0 = the kernels' default)
   int32_t sgd_slots = 0;        // block slots per CTA of the SGD kernel (0 = as many as fit)
+  int32_t sgd_groups = 0;       // consumer/producer groups per CTA of the SGD kernel (0 = as many as fit)
   int32_t test_withhold = 0;    // test hook: the SGD kernel never announces its first finished block
 };
 
@@ -171,6 +172,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Ratings per chunk of the SGD item chain (sgd.cu; the chunk layout is built by train.cu).
 constexpr int SGD_CH = 8;
+constexpr int SGD_MAX_GROUPS = 3;   // consumer/producer groups per CTA of the SGD kernel, at most
+constexpr int SGD_MAX_SLOTS = 4;    // blocks of the schedule in flight per CTA, at most
 
 // Query pairs reduced by one CTA of the caller-scratch RMSE (train.cu).
 constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;

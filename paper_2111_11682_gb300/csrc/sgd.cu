@@ -59,11 +59,11 @@ namespace lshmf {
 constexpr int64_t SGD_DEFAULT_POLLS = int64_t(1) << 22;   // polls of a bounded spin (with back-off: over a second)
 constexpr unsigned SGD_SUSPEND_NS = 1000; // suspend-time hint of one try
 constexpr int CH = SGD_CH;    // ratings per chunk (the chunk layout of prepare_training uses the same size)
-constexpr int GP = 3;         // producer warps per group
-constexpr int NRING = 4;      // chunk buffers per group
+constexpr int GP = 4;         // producer warps per group
+constexpr int NRING = 5;      // chunk buffers per group
 constexpr int GQN = 32;       // group segment list (ring)
-constexpr int MAX_GROUPS = 4;
-constexpr int MAX_SLOTS = 4;  // blocks in flight per CTA
+constexpr int MAX_GROUPS = SGD_MAX_GROUPS;
+constexpr int MAX_SLOTS = SGD_MAX_SLOTS;  // blocks in flight per CTA
 
 static_assert(NRING > 1 && GQN >= NRING + GP + 2, "group segment ring too small");
 
@@ -894,12 +894,13 @@ __global__ void k_sum_seg_sq(const double *x, int64_t n, double *out) {
 
 template <int FPL, int KPL>
 static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
-  // groups and block slots: as many as fit
+  // groups and block slots: as asked, else as many as fit
   const size_t gsz = sizeof(Group<FPL, KPL>);
   auto need = [&](int ng, int ns) {
     return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + 2 * sizeof(int) * size_t(ns) * a.maxu;
   };
-  int ng = MAX_GROUPS, ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : MAX_SLOTS;
+  int ng = h->sgd_groups > 0 ? std::min(h->sgd_groups, MAX_GROUPS) : MAX_GROUPS;
+  int ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : MAX_SLOTS;
   while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
   while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
   if (need(ng, ns) > size_t(h->smem_optin))

@@ -26,7 +26,7 @@ SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "
            "lshmf_batch_create", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
 
 GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
-OPT_MEMORY_LIMIT, OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD = 1, 2, 3, 4
+OPT_MEMORY_LIMIT, OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD, OPT_SGD_GROUPS = 1, 2, 3, 4, 5
 
 
 class LshmfError(RuntimeError):
@@ -209,7 +209,8 @@ class LshMF:
         self._chk(self.lib.lshmf_check(self.h, _stream(stream)))
 
     def set_option(self, option: int, value: int):
-        """lshmf_set_option: OPT_MEMORY_LIMIT (bytes), OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD."""
+        """lshmf_set_option: OPT_MEMORY_LIMIT (bytes), OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_SGD_GROUPS,
+        OPT_TEST_WITHHOLD."""
         self._chk(self.lib.lshmf_set_option(self.h, option, int(value)))
 
     def csc_from_coo(self, i, j, r, stream=None):
@@ -477,6 +478,32 @@ def autotune_P(cfg: Config, i, j, r, nbr, params: Params, candidates=(4, 8, 16, 
     if best is None:
         raise ValueError("autotune_P: no candidate P fits")
     return best[1], best[2], timings
+
+
+def autotune_tile(m: "LshMF", params: Params, tiles=((3, 0), (2, 0), (1, 0), (1, 1)), reps=2, stream=None):
+    """The SGD kernel's tile for a prepared model: times one epoch at each (groups, slots) of the
+    kernel's CTA (groups of one consumer and four producer warps, blocks in flight; 0 = as many as fit)
+    on a scratch copy of the parameters, keeps the fastest on the model (OPT_SGD_GROUPS, OPT_SGD_SLOTS;
+    the result does not depend on the tile) and returns (tile, {tile: epoch ms})."""
+    timings = {}
+    for g, sl in tiles:
+        m.set_option(OPT_SGD_GROUPS, g)
+        m.set_option(OPT_SGD_SLOTS, sl)
+        p = params.clone()
+        ms = []
+        for k in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.train_epoch(p, 0, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if k > 0:
+                ms.append(a.elapsed_time(b))
+        timings[(g, sl)] = sorted(ms)[len(ms) // 2]
+    best = min(timings, key=lambda t: (timings[t], t))
+    m.set_option(OPT_SGD_GROUPS, best[0])
+    m.set_option(OPT_SGD_SLOTS, best[1])
+    return best, timings
 
 
 def plain_mf_config(cfg: Config) -> Config:

@@ -56,3 +56,15 @@ def test_null_handle_is_einval():
     assert lib.lshmf_check(None, None) == lshmf.EINVAL
     assert lib.lshmf_last_error(None) == b"null handle"
     assert lib.lshmf_launch_count() >= 0
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, options and generator ids the binding uses are the header's #define values."""
+    src = open(os.path.join(ROOT, "include", "lshmf.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+LSHMF_([A-Z0-9_]+)\s+(-?\d+)\b", src)}
+    opts = {k[4:]: v for k, v in defs.items() if k.startswith("OPT_")}
+    assert opts == {"MEMORY_LIMIT": pkg.OPT_MEMORY_LIMIT, "WAIT_POLLS": pkg.OPT_WAIT_POLLS,
+                    "SGD_SLOTS": pkg.OPT_SGD_SLOTS, "TEST_WITHHOLD": pkg.OPT_TEST_WITHHOLD,
+                    "SGD_GROUPS": pkg.OPT_SGD_GROUPS}
+    gens = {k: v for k, v in defs.items() if k.startswith("GEN_")}
+    assert gens == {"GEN_RAND": pkg.GEN_RAND, "GEN_RPCOS": pkg.GEN_RPCOS, "GEN_MINHASH": pkg.GEN_MINHASH}

@@ -97,3 +97,54 @@ def test_autotune_returns_a_prepared_model(instances):
     tuned.train_epoch(q, 0)
     tuned.check()
     tuned.close()
+
+
+# (users, items, ratings, P, groups, slots) of instances shaped like the batched multi-instance workload
+C5_SHAPES = [(1000, 500, 10_000, 4, 1, 0), (2500, 900, 40_000, 8, 2, 2), (4000, 1500, 90_000, 16, 3, 1)]
+
+
+def test_c5_shaped_batch_matches_the_oracle():
+    """Instances of the batched workload's shape (F = 32, K = 16, simLSH neighbours from L = 8 tables of
+    8 bits, beta = 0.3) at different P and SGD tiles, trained two epochs in one graph on two branches;
+    each against the FP64 oracle: neighbours bit-exact, per group max |gpu - oracle| <= 1e-4 max
+    |oracle| after both epochs."""
+    import os
+
+    import oracle
+    from paper_2111_11682_gb300 import OPT_SGD_GROUPS, OPT_SGD_SLOTS
+    from test_gpu_parity import PARAM_RTOL, compare_params, oracle_nbr
+
+    E = 2
+    runs = []
+    for x, (M, N, nnz, P, g, sl) in enumerate(C5_SHAPES):
+        w = replace(synth.TINY, name=f"c5-{x}", M=M, N=N, nnz=nnz, P=P, F=32, K=16, L=8, bits=8, beta=0.3,
+                    seed=500 + x, test_frac=0.0)
+        d = synth.generate(w)
+        m = LshMF(config_from_workload(w))
+        m.set_option(OPT_SGD_GROUPS, g)
+        m.set_option(OPT_SGD_SLOTS, sl)
+        ti, tj, tr = T(d["train_i"], torch.int32), T(d["train_j"], torch.int32), T(d["train_r"], torch.uint8)
+        col_ptr, row, rc = m.csc_from_coo(ti, tj, tr)
+        nbr = m.build_neighbours(col_ptr, row, rc, T(d["H"].view(np.int64), torch.int64))
+        _, _, onbr = oracle_nbr(w, d)
+        assert np.array_equal(nbr.cpu().numpy(), onbr), w.name
+        mu = m.prepare_training(ti, tj, tr, nbr)
+        p = Params.from_init(d["U0"], d["V0"], w.K, "cuda:0")
+        p.mu = mu
+        runs.append((w, d, m, p, onbr, mu))
+    b = Batch([r[2] for r in runs], [r[3] for r in runs], epoch0=0, epochs=E, branches=2)
+    b.run()
+    b.check()
+    prev = oracle.set_threads(os.cpu_count() or 1)
+    try:
+        for w, d, m, p, onbr, mu in runs:
+            cfg = oracle.cfg_from_workload(w, w.P)
+            po = oracle.Params.init(d["U0"], d["V0"], w.K)
+            for e in range(E):
+                oracle.train(cfg, d["train_i"], d["train_j"], d["train_r"], onbr, mu, po, e)
+            compare_params(p, po, rtol=PARAM_RTOL, what=f"{w.name} after {E} epochs in the batch")
+    finally:
+        oracle.set_threads(prev)
+    b.close()
+    for r in runs:
+        r[2].close()

@@ -7,14 +7,15 @@
     LSHMF_OPT_TEST_WITHHOLD hook) runs out under a small poll limit; the kernel
     returns, the status reaches the host and the handle recovers.
   - Bad option values are rejected (EINVAL).
-  - The number of block slots per CTA of the SGD kernel does not change the result.
+  - The numbers of block slots and of consumer/producer groups per CTA of the SGD kernel do not
+    change the result.
 """
 import numpy as np
 import pytest
 import torch
 
 import synth
-from paper_2111_11682_gb300 import (OPT_MEMORY_LIMIT, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD, OPT_WAIT_POLLS, LshMF,
+from paper_2111_11682_gb300 import (OPT_MEMORY_LIMIT, OPT_SGD_GROUPS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD, OPT_WAIT_POLLS, LshMF,
                                     LshmfError, Params, config_from_workload, launch_count, lshmf)
 
 pytestmark = pytest.mark.gpu
@@ -61,8 +62,8 @@ def test_memory_limit_gives_enomem_before_any_launch(tiny):
 
 def test_bad_option_values_are_rejected(tiny):
     m = LshMF(config_from_workload(tiny["w"]))
-    for opt, val in ((OPT_MEMORY_LIMIT, -1), (OPT_WAIT_POLLS, -5), (OPT_SGD_SLOTS, 9), (OPT_TEST_WITHHOLD, 2),
-                     (99, 0)):
+    for opt, val in ((OPT_MEMORY_LIMIT, -1), (OPT_WAIT_POLLS, -5), (OPT_SGD_SLOTS, 9), (OPT_SGD_GROUPS, 4),
+                     (OPT_SGD_GROUPS, -1), (OPT_TEST_WITHHOLD, 2), (99, 0)):
         with pytest.raises(LshmfError) as e:
             m.set_option(opt, val)
         assert e.value.status == lshmf.EINVAL
@@ -115,4 +116,19 @@ def test_block_slots_do_not_change_the_result(tiny, slots):
     m.check()
     for name in ("U", "V", "b", "bh", "W", "C"):
         assert torch.equal(getattr(p, name), getattr(ref, name)), (slots, name)
+    m.close()
+
+
+@pytest.mark.parametrize("groups,slots", [(1, 1), (1, 4), (2, 2), (3, 1)])
+def test_groups_and_slots_do_not_change_the_result(tiny, groups, slots):
+    """One to three groups of one consumer and four producer warps per CTA, with one to four blocks in
+    flight: the same parameters, bit for bit, after two epochs."""
+    m = LshMF(config_from_workload(tiny["w"]))
+    ref = _train(m, tiny, 2)
+    m.set_option(OPT_SGD_GROUPS, groups)
+    m.set_option(OPT_SGD_SLOTS, slots)
+    p = _train(m, tiny, 2)
+    m.check()
+    for name in ("U", "V", "b", "bh", "W", "C"):
+        assert torch.equal(getattr(p, name), getattr(ref, name)), (groups, slots, name)
     m.close()
