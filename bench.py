@@ -571,7 +571,7 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
            "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
            "instances": n_inst, "ratings": int(sum(nnz_all)), "epochs": E,
            "P_histogram": {str(k): int(v) for k, v in zip(*np.unique([m.cfg.P for m in models], return_counts=True))},
-           "tile_histogram (groups, slots; 0 = as many as fit)": {
+           "tile_histogram (groups, slots; 0 = the kernel's default)": {
                str(k): int(v) for k, v in zip(*np.unique(["%d,%d" % t for t in tiles], return_counts=True))},
            "moved_to_fastest_P": moved, "setup_s": round(setup_s, 1), "modes": {}}
     out["sm_time_bound_ms"] = round(E * sum(c * min(m.cfg.P, sms) for c, m in zip(costs, models)) / sms, 2)
@@ -638,15 +638,46 @@ def sgd_roofline(stats, w, epoch_ms, P):
             "epoch_ms_median": round(ep_med, 3), "P": P, "note": f"frac of {peak_kind} HBM copy bandwidth"}
 
 
+# P and SGD tile candidates the bench's autotuner tries per workload (others: the workload's P only)
+P_CANDIDATES = {"mid-480kx17770-100M": (1216, 1824), "large-1Mx625k-250M": (304, 608)}
+TILE_CANDIDATES = ((3, 2), (3, 3), (3, 4))
+
+
+def tune_job(w, dv, dev, candidates=None, tiles=TILE_CANDIDATES):
+    """Untimed autotuning before the timed jobs: the workload's neighbours once, then autotune_P over
+    the candidate P (fastest epoch) and autotune_tile over the SGD kernel's (groups, slots) at that P.
+    Returns (P, tile, {"P_ms": {P: epoch ms}, "tile_ms": {tile: epoch ms}})."""
+    from paper_2111_11682_gb300 import LshMF, Params, autotune_P, autotune_tile, config_from_workload
+
+    candidates = candidates or P_CANDIDATES.get(w.name, (w.P,))
+    m0 = LshMF(config_from_workload(w))
+    col_ptr, row, rc = m0.csc_from_coo(dv["train_i"], dv["train_j"], dv["train_r"])
+    nbr = m0.build_neighbours(col_ptr, row, rc, dv["H"])
+    del col_ptr, row, rc
+    p0 = Params.from_init(dv["U0"], dv["V0"], w.K, dev)
+    m, mu, pt = autotune_P(m0.cfg, dv["train_i"], dv["train_j"], dv["train_r"], nbr, p0, candidates=candidates,
+                           objective="latency", reps=1)
+    m0.close()
+    p0.mu = mu
+    tile, tt = autotune_tile(m, p0, tiles=tiles, reps=1)
+    P = m.cfg.P
+    m.close()
+    del nbr, p0
+    return P, tile, {"P_ms": {str(k): (None if v is None else round(v, 2)) for k, v in pt.items()},
+                     "tile_ms": {"%d,%d" % k: round(v, 2) for k, v in tt.items()}}
+
+
 class Job:
     """One whole training job through the library on device-resident inputs: COO -> CSC, simLSH
     neighbour build, training layout, every epoch, held-out RMSE."""
 
-    def __init__(self, w, P, dv, dev, epochs):
-        from paper_2111_11682_gb300 import LshMF, Params, config_from_workload
+    def __init__(self, w, P, dv, dev, epochs, tile=(0, 0)):
+        from paper_2111_11682_gb300 import OPT_SGD_GROUPS, OPT_SGD_SLOTS, LshMF, Params, config_from_workload
 
         self.w, self.P, self.dv, self.E = w, P, dv, epochs
         self.m = LshMF(config_from_workload(w, P))
+        self.m.set_option(OPT_SGD_GROUPS, tile[0])
+        self.m.set_option(OPT_SGD_SLOTS, tile[1])
         self.init = Params.from_init(dv["U0"], dv["V0"], w.K, dev)
         self.p = self.init.clone()
         self.epoch_events = []
@@ -704,7 +735,9 @@ def measure_large(dev, steps=2, warmup=1):
     host, dv = upload(d, dev, pin=False)
     del host
     stream = torch.cuda.current_stream()
-    job = Job(w, w.P, dv, dev, w.epochs)
+    P, tile, tuned = tune_job(w, dv, dev)
+    torch.cuda.empty_cache()
+    job = Job(w, P, dv, dev, w.epochs, tile)
     jobs_ms = []
     for k in range(warmup + steps):
         torch.cuda.synchronize()
@@ -734,12 +767,13 @@ def measure_large(dev, steps=2, warmup=1):
         oracle.set_threads(prev)
     rm_g = gpu_job_rmse(ws, ds, dev)
     return {"workload": w.name, "M": w.M, "N": w.N, "nnz_train": nnz, "F": w.F, "K": w.K, "L": w.L,
-            "bits": w.bits, "psi_pow": w.psi_pow, "epochs": w.epochs, "P": w.P,
+            "bits": w.bits, "psi_pow": w.psi_pow, "epochs": w.epochs, "P": P, "sgd_tile": list(tile),
+            "autotune": tuned,
             "value": w.epochs * nnz / (ms / 1e3), "unit": "rating-updates/s", "ms_per_job": round(ms, 2),
             "jobs_ms": [round(x, 2) for x in jobs_ms], "rmse_heldout": rm,
             "epoch_rating_updates_per_s": nnz / (float(np.median(epoch_ms)) / 1e3),
             "epoch_ms_first_and_later": [None if v is None else round(v, 3) for v in epoch_split(epoch_ms, w.epochs)],
-            "roofline": {"sgd": sgd_roofline(stats, w, epoch_ms, w.P), "signatures": sig["roofline"]},
+            "roofline": {"sgd": sgd_roofline(stats, w, epoch_ms, P), "signatures": sig["roofline"]},
             "signatures": {k: v for k, v in sig.items() if k != "roofline"},
             "rmse_parity": rmse_parity(rm_g, rm_o, ws.name), "layout": stats, "generate_s": round(gen_s, 1)}
 
@@ -764,7 +798,16 @@ def run_ours(args, rank, world, local_rank):
     nnz = len(d["train_i"])
     host, dv = upload(d, dev)
     stream = torch.cuda.current_stream()
-    job = Job(w, P, dv, dev, E)
+    tile, tuned = (0, 0), None
+    if not args.P:            # P and the SGD tile autotuned (untimed) unless P is given
+        P, tile, tuned = tune_job(w, dv, dev)
+        torch.cuda.empty_cache()
+        if world > 1:         # every replica takes rank 0's choice
+            import torch.distributed as dist
+            ch = torch.tensor([P, tile[0], tile[1]], dtype=torch.int64, device=dev)
+            dist.broadcast(ch, 0)
+            P, tile = int(ch[0]), (int(ch[1]), int(ch[2]))
+    job = Job(w, P, dv, dev, E, tile)
     m, p = job.m, job.p
 
     def job_e2e():
@@ -844,7 +887,8 @@ def run_ours(args, rank, world, local_rank):
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (SGD), int32/int64 (simLSH)", "data": "synthetic (seeded generator, %s)" % w.name,
            "config": {"workload": w.name, "M": w.M, "N": w.N, "nnz_train": nnz, "F": w.F, "K": w.K, "L": w.L,
-                      "bits": w.bits, "psi_pow": w.psi_pow, "epochs": E, "P": P,
+                      "bits": w.bits, "psi_pow": w.psi_pow, "epochs": E, "P": P, "sgd_tile": list(tile),
+                      "autotune": tuned,
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs > L2 (ratings ~%.0f MB)" % (nnz * 9 / 1e6)},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,

@@ -119,8 +119,8 @@ int64_t lshmf_launch_count(void);
  *      gives up makes the kernel return and the next synchronising call report
  *      LSHMF_ETIMEOUT.  Range [0, 2^30].
  *  LSHMF_OPT_SGD_SLOTS     blocks of the schedule held at once by one CTA of the
- *      SGD kernel (0 = as many as fit in shared memory, at most 4).  The result
- *      does not depend on it.
+ *      SGD kernel, 1-4 (0 = the default, 2; fewer if shared memory is short).
+ *      The result does not depend on it.
  *  LSHMF_OPT_SGD_GROUPS    consumer/producer groups (one consumer and four
  *      producer warps each) per CTA of the SGD kernel (0 = as many as fit in
  *      shared memory, at most 3).  The result does not depend on it.

@@ -174,6 +174,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 constexpr int SGD_CH = 8;
 constexpr int SGD_MAX_GROUPS = 3;   // consumer/producer groups per CTA of the SGD kernel, at most
 constexpr int SGD_MAX_SLOTS = 4;    // blocks of the schedule in flight per CTA, at most
+constexpr int SGD_DEFAULT_SLOTS = 2;  // and by default (the fastest on the Netflix and Yahoo! shapes)
 
 // Query pairs reduced by one CTA of the caller-scratch RMSE (train.cu).
 constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;

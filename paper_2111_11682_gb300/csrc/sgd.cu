@@ -894,13 +894,13 @@ __global__ void k_sum_seg_sq(const double *x, int64_t n, double *out) {
 
 template <int FPL, int KPL>
 static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
-  // groups and block slots: as asked, else as many as fit
+  // groups and block slots: as asked, else as many groups as fit and SGD_DEFAULT_SLOTS slots
   const size_t gsz = sizeof(Group<FPL, KPL>);
   auto need = [&](int ng, int ns) {
     return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + 2 * sizeof(int) * size_t(ns) * a.maxu;
   };
   int ng = h->sgd_groups > 0 ? std::min(h->sgd_groups, MAX_GROUPS) : MAX_GROUPS;
-  int ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : MAX_SLOTS;
+  int ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : SGD_DEFAULT_SLOTS;
   while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
   while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
   if (need(ng, ns) > size_t(h->smem_optin))

@@ -482,7 +482,7 @@ def autotune_P(cfg: Config, i, j, r, nbr, params: Params, candidates=(4, 8, 16, 
 
 def autotune_tile(m: "LshMF", params: Params, tiles=((3, 0), (2, 0), (1, 0), (1, 1)), reps=2, stream=None):
     """The SGD kernel's tile for a prepared model: times one epoch at each (groups, slots) of the
-    kernel's CTA (groups of one consumer and four producer warps, blocks in flight; 0 = as many as fit)
+    kernel's CTA (groups of one consumer and four producer warps, blocks in flight; 0 = the default)
     on a scratch copy of the parameters, keeps the fastest on the model (OPT_SGD_GROUPS, OPT_SGD_SLOTS;
     the result does not depend on the tile) and returns (tile, {tile: epoch ms})."""
     timings = {}
