@@ -325,7 +325,8 @@ def measure_ingest(w, d, P, dev, reps=3, frac=0.01, local_epochs=1):
             "ratings_per_s": n / (ms / 1e3)}
 
 
-def measure_serving(w, d, P, dev, frac_users=0.02, frac_items=0.01, rate=4000.0, horizon=4.0, seed=1):
+def measure_serving(w, d, P, dev, frac_users=0.02, frac_items=0.01, rate=4000.0, horizon=4.0, seed=1,
+                    users=(1, 16), loguniform=False):
     """Serving loop (serve.Server) under a Poisson mix on the workload: top-N queries of 1-16 users
     (mode 1, top-10) arrive at `rate` per second for `horizon` seconds, and the last `frac_users` of
     users and `frac_items` of items arrive as online updates of lognormal size (median 20k ratings,
@@ -379,7 +380,12 @@ def measure_serving(w, d, P, dev, frac_users=0.02, frac_items=0.01, rate=4000.0,
         incs.append((Mb[k] - prevM, Nb[k] - prevN, i[sel], j[sel], r[sel]))
         prevM, prevN = Mb[k], Nb[k]
     qt = poisson_times(rate, horizon, rng)
-    qusers = [rng.integers(0, M_old, rng.integers(1, 17)).astype(np.int32) for _ in qt]
+    lo, hi = users
+    if loguniform:          # query sizes log-uniform in [lo, hi]
+        qsize = lambda: int(np.exp(rng.uniform(np.log(lo), np.log(hi + 1))))
+    else:
+        qsize = lambda: int(rng.integers(lo, hi + 1))
+    qusers = [rng.integers(0, M_old, min(hi, max(lo, qsize()))).astype(np.int32) for _ in qt]
     ut = np.sort(rng.uniform(0.05, horizon, nk))
     events = sorted([(x, 0, q) for q, x in enumerate(qt)] + [(x, 1, k) for k, x in enumerate(ut)])
     srv = Server(m, p, H, nbr, n=10, mode=1, max_users=4096, depth=4)
@@ -418,7 +424,8 @@ def measure_serving(w, d, P, dev, frac_users=0.02, frac_items=0.01, rate=4000.0,
     # queries answered while some update was running (submitted after its start, answered before its end)
     spans = [(u.done - u.latency, u.done) for u in ureq if u.error is None]
     during = sum(1 for q in qreq if q.error is None and any(a < q.arrival and q.done < b for a, b in spans))
-    out = {"what": "serve.Server: Poisson top-N queries (1-16 users, mode 1, top-10) + online updates of lognormal "
+    out = {"what": "serve.Server: Poisson top-N queries (%d-%d users%s, mode 1, top-10) + online updates of lognormal "
+                   % (lo, hi, ", log-uniform" if loguniform else "") +
                    "size, queries served from the last published model while updates run",
            "rate_per_s": rate, "horizon_s": horizon, "updates": nk,
            "update_ratings": [int(len(x[2])) for x in incs],
@@ -868,11 +875,12 @@ def run_ours(args, rank, world, local_rank):
         del col_ptr, row, rc
     if rank == 0 and not args.no_serving:
         topn = measure_topn(m, p, w, dev)
-    ingest = serving = generators = batch = large = None
+    ingest = serving = serving_uneven = generators = batch = large = None
     if rank == 0 and not args.no_serving:
         m.close()
         ingest = measure_ingest(w, d, P, dev)
         serving = measure_serving(w, d, P, dev)
+        serving_uneven = measure_serving(w, d, P, dev, rate=800.0, users=(1, 4096), loguniform=True, seed=2)
         generators = measure_generators(w, d, P, dev)
         batch = measure_batch(dev)
     m.close()
@@ -895,7 +903,8 @@ def run_ours(args, rank, world, local_rank):
            "rmse_heldout": rmse, "epoch_rating_updates_per_s": nnz / (float(np.median(epoch_ms)) / 1e3),
            "epoch_ms_first_and_later": [None if v is None else round(v, 3) for v in epoch_split(epoch_ms, E)],
            "layout": stats, "signatures": signatures,
-           "topn": topn, "ingest": ingest, "serving": serving, "generators": generators, "batch": batch,
+           "topn": topn, "ingest": ingest, "serving": serving,
+           "serving_uneven_queries": serving_uneven, "generators": generators, "batch": batch,
            "large": large, "generate_s": round(gen_s, 1)}
     if rank == 0 and not args.no_cpu:
         ws = synth.scaled(w, 0.005)
