@@ -646,7 +646,7 @@ def sgd_roofline(stats, w, epoch_ms, P):
 
 
 # P and SGD tile candidates the bench's autotuner tries per workload (others: the workload's P only)
-P_CANDIDATES = {"mid-480kx17770-100M": (1216, 1824), "large-1Mx625k-250M": (304, 608)}
+P_CANDIDATES = {"mid-480kx17770-100M": (912, 1216, 1824), "large-1Mx625k-250M": (608, 1216, 1824)}
 TILE_CANDIDATES = ((3, 2), (3, 3), (3, 4))
 
 

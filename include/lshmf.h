@@ -119,13 +119,13 @@ int64_t lshmf_launch_count(void);
  *      gives up makes the kernel return and the next synchronising call report
  *      LSHMF_ETIMEOUT.  Range [0, 2^30].
  *  LSHMF_OPT_SGD_SLOTS     blocks of the schedule held at once by one CTA of the
- *      SGD kernel, 1-4 (0 = the default, 2; fewer if shared memory is short).
+ *      SGD kernel, 1-4 (0 = the default, 3; fewer if shared memory is short).
  *      The result does not depend on it.
  *  LSHMF_OPT_SGD_GROUPS    consumer/producer groups (one consumer and four
  *      producer warps each) per CTA of the SGD kernel (0 = as many as fit in
  *      shared memory, at most 3).  The result does not depend on it.
  *  LSHMF_OPT_TEST_WITHHOLD test hook, 1 = the SGD kernel never tells the first
- *      pipeline of each CTA that the stratum's work is all handed out, so its
+ *      pipeline of each CTA that the epoch's work is all handed out, so its
  *      producers wait for a flag that nothing sets until their poll limit runs
  *      out (with a small LSHMF_OPT_WAIT_POLLS the call returns LSHMF_ETIMEOUT
  *      quickly); 0 = off.  The parameters are then undefined. */
@@ -227,8 +227,10 @@ lshmf_status lshmf_prepare_training(lshmf_handle *h, const int32_t *d_i, const i
  * gamma_g = alpha_g / (1 + beta * epoch^1.5) (Eq. 7, epoch counted from 0).
  * The baseline of a neighbour inside term (2) uses the current b_i and the
  * neighbour's bhat as it was when the epoch started.  An empty R^K or N^K
- * contributes 0 and leaves its parameters unchanged.  The result is
- * deterministic and independent of launch order inside a stratum.
+ * contributes 0 and leaves its parameters unchanged.  The result is that of
+ * running the strata one after another, deterministic and independent of
+ * timing (one kernel launch per epoch starts a block as soon as the blocks of
+ * the previous stratum that share its items or users are finished).
  * h_sq_err: if not NULL, receives sum of e^2 over the epoch (scaled units)
  * and the call synchronises.  Requires lshmf_prepare_training. */
 lshmf_status lshmf_train_epoch(lshmf_handle *h, const lshmf_params *p, int32_t epoch,

@@ -83,7 +83,8 @@ struct TrainLayout {
   DevBuf seg_sq;    // double [nseg]: per-run sum of e^2
   DevBuf seg_ck;    // int32  [nseg + 1]: first chunk of each run (chunks of SGD_CH ratings)
   DevBuf ck_roff;   // int64  [chunks]: offset of each chunk's packed neighbour values
-  DevBuf df;        // int32  [P]: blocks of each stratum taken so far (SGD scheduler)
+  DevBuf df;        // int32  [16 + P x P]: [0] blocks of the epoch taken so far, from [16] one flag per
+                    //        (stratum, item block) set once the block is finished (SGD scheduler)
   int64_t nchunks = 0;
 };
 
@@ -174,7 +175,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 constexpr int SGD_CH = 8;
 constexpr int SGD_MAX_GROUPS = 3;   // consumer/producer groups per CTA of the SGD kernel, at most
 constexpr int SGD_MAX_SLOTS = 4;    // blocks of the schedule in flight per CTA, at most
-constexpr int SGD_DEFAULT_SLOTS = 2;  // and by default (the fastest on the Netflix and Yahoo! shapes)
+constexpr int SGD_DEFAULT_SLOTS = 3;  // and by default (within 1 % of the fastest on the Netflix and Yahoo! shapes)
+// Bytes of the SGD scheduler's epoch counter and per-block finished flags.
+inline size_t sgd_flags_bytes(int64_t P) { return sizeof(int32_t) * size_t(16 + P * P); }
 
 // Query pairs reduced by one CTA of the caller-scratch RMSE (train.cu).
 constexpr int64_t RMSE_PAIRS_PER_CTA = 2048;

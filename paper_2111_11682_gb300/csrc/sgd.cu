@@ -7,9 +7,21 @@
 // values the sequential order gives it: its item's parameters after the item's
 // previous rating, its user's after the user's previous rating.
 //
-// Execution.  One launch per stratum with one persistent CTA per SM.  A CTA's
-// scheduler warp takes the stratum's blocks from a global counter (heaviest
-// first), loads a block's user table into a free block slot and hands the
+// Execution.  One launch per epoch with one persistent CTA per SM (at most P).
+// A CTA's scheduler warp takes blocks from a global counter in stratum order
+// (heaviest first inside a stratum).  Strata need no barrier between them:
+// block (s, q) (item block q, user block (q + s) mod P) shares its items only
+// with the blocks (s', q) and its users only with the blocks (s', q + s - s')
+// of earlier strata s', and block (s - 1, q) follows (s - 2, q) and
+// (s - 2, q + 1) in turn, so block (s, q) may start as soon as blocks
+// (s - 1, q) and (s - 1, q + 1) are finished: by induction every earlier block
+// sharing an item or a user with it is then finished too.  A finished block
+// sets its flag (release at GPU scope, after every consumer's writes of the
+// block); the scheduler waits for the two flags (acquire at GPU scope) before
+// it loads the block.  Blocks are taken in counter order and a block waits
+// only on blocks taken before it, so the oldest unfinished block never waits:
+// the epoch progresses even when not every CTA is resident.  It then loads
+// the block's user table into a free block slot and hands the
 // block's item runs ("segments"), in order, to the CTA's groups of one
 // consumer warp and GP producer warps (each run to the group with the least
 // work not yet consumed).  A group cuts its runs into chunks of at most CH
@@ -82,10 +94,12 @@ struct SgdArgs {
   const int64_t *blk_seg;
   const int64_t *blk_user;
   const int32_t *order;
-  int32_t *next_blk;         // per stratum: blocks taken (zeroed per epoch)
+  int32_t *next_blk;         // [0]: blocks taken this epoch (zeroed per epoch)
+  int32_t *done;             // [P x P]: 1 once block (stratum, item block) is finished (zeroed per epoch)
+  int n_strata;              // strata [0, n_strata) of the epoch run in this launch
   int64_t polls;             // bounded-wait limit (spins)
   int64_t tries;             // bounded-wait limit (suspending mbarrier tries)
-  int withhold;              // test hook: group 0 is never told that the stratum's segments are all handed out
+  int withhold;              // test hook: group 0 is never told that the launch's segments are all handed out
   const int32_t *users;
   const float *bh0n;
   double *seg_sq;
@@ -103,6 +117,12 @@ __device__ __forceinline__ int ld_acq(const int *p) {
 }
 __device__ __forceinline__ void st_rel(int *p, int v) {
   cuda::atomic_ref<int, cuda::thread_scope_block>(*p).store(v, cuda::memory_order_release);
+}
+__device__ __forceinline__ int ld_acq_gpu(const int *p) {
+  return cuda::atomic_ref<const int, cuda::thread_scope_device>(*p).load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void st_rel_gpu(int *p, int v) {
+  cuda::atomic_ref<int, cuda::thread_scope_device>(*p).store(v, cuda::memory_order_release);
 }
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -197,7 +217,7 @@ struct CtaCtl {
   int abort_;
   int pad[7];
   int slot_left[MAX_SLOTS];   // segments of the slot's block not finished (0 = slot free)
-  int slot_pad[MAX_SLOTS];
+  int slot_flag[MAX_SLOTS];   // index of the slot's block in the done flags
 };
 
 struct Smem {
@@ -272,29 +292,50 @@ __device__ __forceinline__ void unlock_warp(int *l) {
 }
 
 // ------------------------------------------------------------ scheduler ----
-// The scheduler warp of a CTA takes the stratum's blocks from a global counter
-// (heaviest first).  For each block it waits for a free block slot, loads the
+// The scheduler warp of a CTA takes the epoch's blocks from a global counter
+// (stratum by stratum, heaviest first inside a stratum).  For each block it
+// waits for the two blocks of the previous stratum it follows (see the top of
+// this file), then for a free block slot, loads the
 // block's user table into the slot and hands the block's segments, in order,
 // to the groups: each segment goes to the group with the fewest chunks not yet
 // consumed among those whose segment ring has room (a ring entry is reused
 // only when every producer of the group has moved past it).  Producers take no
 // lock: they wait for their group's end position to pass theirs.
 template <int FPL, int KPL>
-__device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> *grp, int ng, int s) {
+__device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> *grp, int ng) {
   const int lane = threadIdx.x & 31;
   CtaCtl *ctl = sm.ctl;
   int endp[MAX_GROUPS], nseg[MAX_GROUPS];
   for (int g = 0; g < MAX_GROUPS; ++g) endp[g] = nseg[g] = 0;
   bool ok = true;
   while (ok) {
-    int bi = 0;
-    if (lane == 0) bi = atomicAdd(&a.next_blk[s], 1);
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (bi >= a.P) break;
-    const int q = a.order[int64_t(s) * a.P + bi];
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.next_blk[0], 1);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= a.n_strata * a.P) break;
+    const int s = idx / a.P;
+    const int q = a.order[idx];   // order holds, per stratum, its item blocks heaviest first
     const int64_t blk = int64_t(q) * a.P + (q + s) % a.P;
+    const int flag = s * a.P + q;
+    if (s > 0) {   // blocks (s - 1, q) and (s - 1, q + 1) finished
+      int it = 0, ready = 0;
+      while (true) {
+        if (lane == 0)
+          ready = ld_acq_gpu(&a.done[flag - a.P]) != 0 && ld_acq_gpu(&a.done[(s - 1) * a.P + (q + 1) % a.P]) != 0;
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (ready) break;
+        if (++it > a.polls || ld_acq(&ctl->abort_)) {
+          sgd_abort(a, ctl);
+          return;
+        }
+        backoff(it);
+      }
+    }
     const int sg0 = int(a.blk_seg[blk]), sg1 = int(a.blk_seg[blk + 1]);
-    if (sg0 == sg1) continue;
+    if (sg0 == sg1) {   // an empty block is finished once the blocks it follows are
+      if (lane == 0) st_rel_gpu(&a.done[flag], 1);
+      continue;
+    }
     const int64_t u0 = a.blk_user[blk];
     const int nu = int(a.blk_user[blk + 1] - u0);
     const int ns = sg1 - sg0;
@@ -323,7 +364,10 @@ __device__ __noinline__ void scheduler(const SgdArgs &a, const Smem &sm, Group<F
       cn[x] = 0;
     }
     __syncwarp();
-    if (lane == 0) ctl->slot_left[slot] = ns;
+    if (lane == 0) {
+      ctl->slot_flag[slot] = flag;
+      ctl->slot_left[slot] = ns;
+    }
     __threadfence_block();   // the user table and the slot count precede every segment of the block
     __syncwarp();
     for (int x0 = 0; x0 < ns && ok; x0 += 32) {
@@ -401,11 +445,11 @@ struct Producer {
   const SgdArgs &a;
   const Smem &sm;
   Group<FPL, KPL> &G;
-  int s, p;       // stratum, producer index in the group
+  int p;          // producer index in the group
   int cur = 0;    // group segment index holding the current position
 
-  __device__ Producer(const SgdArgs &a_, const Smem &sm_, Group<FPL, KPL> &G_, int s_, int p_)
-      : a(a_), sm(sm_), G(G_), s(s_), p(p_) {}
+  __device__ Producer(const SgdArgs &a_, const Smem &sm_, Group<FPL, KPL> &G_, int p_)
+      : a(a_), sm(sm_), G(G_), p(p_) {}
 
   // Waits until stream position pos is covered by a segment handed to the
   // group.  Returns 1 when it is, 0 when the group's stream ends before pos,
@@ -653,8 +697,8 @@ struct Producer {
 };
 
 template <int FPL, int KPL>
-__device__ void producer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G, int s, int p) {
-  Producer<FPL, KPL> pr(a, sm, G, s, p);
+__device__ void producer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G, int p) {
+  Producer<FPL, KPL> pr(a, sm, G, p);
   for (int pos = p;; pos += GP) {
     const int c = pr.cover(pos);
     if (c < 0) return;
@@ -822,8 +866,14 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
     const int slot = C.slot;
     __syncwarp();
     if (lane == 0 && (flags & FL_LAST)) {
+      const int bflag = ctl->slot_flag[slot];
       __threadfence_block();   // the block's releases above precede the slot's reuse
-      atomicSub(&ctl->slot_left[slot], 1);
+      if (atomicSub(&ctl->slot_left[slot], 1) == 1) {
+        // the block's last run: every consumer's writes of the block (ordered before their own
+        // decrements) precede its flag, which later strata's blocks acquire at GPU scope
+        __threadfence();
+        st_rel_gpu(&a.done[bflag], 1);
+      }
     }
     mbar_arrive(&G.empty[buf]);   // every lane's reads of the chunk are done
     if (lane == 0) st_rel(&G.cpos, pos + 1);
@@ -832,7 +882,7 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
 
 template <int FPL, int KPL>
 __global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
-k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
+k_sgd_epoch(const SgdArgs a, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
   // carve shared memory: [groups][ctl][qt][users][cnt]
@@ -864,12 +914,12 @@ k_sgd_stratum(const SgdArgs a, int s, int ngroups) {
   // warps 0..ngroups-1 are the consumers (one per warp scheduler), then the
   // producers, then the block scheduler
   if (wid == ngroups * (GP + 1)) {
-    scheduler<FPL, KPL>(a, sm, grp, ngroups, s);
+    scheduler<FPL, KPL>(a, sm, grp, ngroups);
   } else if (wid < ngroups) {
     consumer<FPL, KPL>(a, sm, grp[wid]);
   } else if (wid < ngroups * (GP + 1)) {
     const int pw = wid - ngroups;
-    producer<FPL, KPL>(a, sm, grp[pw % ngroups], s, pw / ngroups);
+    producer<FPL, KPL>(a, sm, grp[pw % ngroups], pw / ngroups);
   }
 }
 
@@ -910,11 +960,11 @@ static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream
   // the attribute is a per-kernel cap shared by every handle: set it to the device maximum so that
   // launches of handles with different block sizes (captured together into one graph, or issued from
   // several threads) never see another handle's smaller cap
-  LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_stratum<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  LSHMF_CUDA(h, cudaFuncSetAttribute(k_sgd_epoch<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      h->smem_optin));
   const int grid = std::min(h->num_sms, a.P);
-  for (int s = 0; s < n_strata; ++s)
-    LSHMF_LAUNCH(h, (k_sgd_stratum<FPL, KPL>), grid, 32 * (ng * (GP + 1) + 1), smem, st, a, s, ng);
+  a.n_strata = n_strata;
+  if (n_strata > 0) LSHMF_LAUNCH(h, (k_sgd_epoch<FPL, KPL>), grid, 32 * (ng * (GP + 1) + 1), smem, st, a, ng);
   return LSHMF_OK;
 }
 
@@ -932,7 +982,8 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.N * c.K, 256), 16L * h->num_sms));
   LSHMF_LAUNCH(h, k_gather_bh0n, g, 256, 0, st, tl.bh0.as<float>(), tl.nbr.as<int32_t>(), c.N * c.K,
                tl.bh0n.as<float>());
-  LSHMF_CUDA(h, cudaMemsetAsync(tl.df.p, 0, size_t(c.P) * 4, st));
+  // the epoch's block counter and per-block finished flags start at zero
+  LSHMF_CUDA(h, cudaMemsetAsync(tl.df.p, 0, sgd_flags_bytes(c.P), st));
   if (h_sq) LSHMF_CUDA(h, cudaMemsetAsync(tl.seg_sq.p, 0, tl.nseg * 8, st));
   SgdArgs a;
   a.sr = tl.sr.as<uint32_t>();
@@ -947,6 +998,7 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   a.blk_user = tl.blk_user.as<int64_t>();
   a.order = tl.blk_order.as<int32_t>();
   a.next_blk = tl.df.as<int32_t>();
+  a.done = tl.df.as<int32_t>() + 16;
   a.users = tl.users.as<int32_t>();
   a.bh0n = tl.bh0n.as<float>();
   a.seg_sq = tl.seg_sq.as<double>();

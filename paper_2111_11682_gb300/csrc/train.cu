@@ -9,10 +9,12 @@
 //   rating, a K-bit mask (bit k: J^K[j][k] in R(i)) and, packed per rating,
 //   the ratings r_{i, J^K[j][k]} of the set bits.
 //
-// SGD epoch (sgd.cu): one launch per stratum; a CTA's scheduler warp takes the
-// stratum's blocks from a counter and hands their item runs, cut into chunks
-// of SGD_CH ratings, to its groups of warps; a chunk's users must have finished
-// their earlier ratings of the block (per-user counters in shared memory).
+// SGD epoch (sgd.cu): one launch per epoch; a CTA's scheduler warp takes the
+// blocks from a counter, stratum by stratum, each once the two blocks of the
+// previous stratum that share its items or its users are finished, and hands
+// their item runs, cut into chunks of SGD_CH ratings, to its groups of warps;
+// a chunk's users must have finished their earlier ratings of the block
+// (per-user counters in shared memory).
 // Every rating therefore reads exactly the values the sequential
 // (stratum, block, j, i) order would give it: the result is that of the
 // sequential schedule, and independent of timing.
@@ -480,12 +482,12 @@ lshmf_status prepare_training(Handle *h, const int32_t *d_i, const int32_t *d_j,
     tl.nchunks = nchunks;
     LSHMF_TRY(ensure(h, tl.seg_ck, (nseg + 1) * 4, "layout run chunks"));
     LSHMF_TRY(ensure(h, tl.ck_roff, nchunks * 8 + 8, "layout chunk offsets"));
-    LSHMF_TRY(ensure(h, tl.df, P * 4, "SGD stratum block counters"));
+    LSHMF_TRY(ensure(h, tl.df, sgd_flags_bytes(P), "SGD block counter and flags"));
     LSHMF_LAUNCH(h, k_chunks, grid_for(h, nseg + 1), 256, 0, st, tl.seg_p0.as<int64_t>(), ckscan, nseg, roff,
                  tl.seg_ck.as<int32_t>(), tl.ck_roff.as<int64_t>());
   }
   LSHMF_TRY(check_device_flag(h, st, "prepare_training"));
-  // per-stratum launch order (heaviest blocks first)
+  // order in which the SGD scheduler takes each stratum's blocks (heaviest first)
   LSHMF_TRY(ensure(h, tl.blk_order, NB * 4, "layout block order"));
   {
     uint64_t *ko = T[22].as<uint64_t>();

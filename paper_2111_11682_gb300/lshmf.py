@@ -407,7 +407,7 @@ def batch_plan(cost, branches):
 def pick_P(timings: dict, objective: str = "sm_time", num_sms: int = 152) -> int:
     """Choice of the autotuner: timings maps P -> measured epoch ms (None where the layout did not
     fit).  "latency": the fastest epoch alone.  "sm_time": the least SM-time, epoch ms x min(P, SMs)
-    (a stratum launch occupies min(P, SMs) SMs), the cost that matters when many instances share the
+    (an epoch launch occupies min(P, SMs) SMs), the cost that matters when many instances share the
     GPU.  Ties go to the smaller P."""
     ok = {P: t for P, t in timings.items() if t is not None}
     if not ok:

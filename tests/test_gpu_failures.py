@@ -80,7 +80,7 @@ def _train(m, tiny, epochs=1):
 
 
 def test_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(tiny):
-    """The test hook withholds the end-of-stratum flag from the first pipeline of every CTA, so its
+    """The test hook withholds the end-of-work flag from the first pipeline of every CTA, so its
     producers wait for a flag nothing sets; with a poll limit of 2,000 their waits run out in well
     under a second, the kernel returns, and the next synchronising call reports LSHMF_ETIMEOUT.  The
     handle then trains normally again after a new prepare."""
