@@ -193,6 +193,11 @@ lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, u
 lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *nbr, cudaStream_t st);
 // Keys (L x N) from pre-sign sums (N x 64W).
 lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, uint32_t *sig, cudaStream_t st);
+// Eq. 3 pre-sign sums (N x 64W, int64) and keys (L x N) of the N columns of a
+// CSC over users [0, M); `what` names the caller in a bad-input error.
+lshmf_status signature_sums(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,
+                            int64_t N, int64_t M, const uint64_t *H, int W, int64_t *sums, uint32_t *sig,
+                            const char *what, cudaStream_t st);
 // Exclusive scan of n int64 values (out may alias in); out[n] = total.
 lshmf_status exclusive_scan_i64(Handle *h, const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
 // Synchronously checks 0 <= x[k] < hi for k < n (EINVAL otherwise).

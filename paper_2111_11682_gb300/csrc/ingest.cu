@@ -57,31 +57,11 @@ __global__ void k_ing_ptr(const uint64_t *ks, int64_t n, uint64_t div, int64_t G
   }
 }
 
-// Hash values of Alg. 4: sums[j][b] += sum over the item's new ratings of
-// Psi(r) (2 H_i[b] - 1).  One warp per item (the increment in item order):
-// lane l accumulates bits l and l + 32 of each 64-bit hash word exactly in
-// int64, then adds once (no other warp touches the item).
-__global__ void k_ing_sums(const int64_t *ni_ptr, const int32_t *ni_i, const uint8_t *ni_r, int64_t Nt,
-                           const uint64_t *H, int hstride, int W, int psi_pow, int64_t *sums) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < Nt;
-       j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    const int64_t p0 = ni_ptr[j], p1 = ni_ptr[j + 1];
-    if (p0 == p1) continue;
-    for (int w = 0; w < W; ++w) {
-      int64_t a0 = 0, a1 = 0;
-      for (int64_t p = p0; p < p1; ++p) {
-        const int64_t i = ni_i[p];
-        int64_t ps = 1;
-        for (int q = 0; q < psi_pow; ++q) ps *= int64_t(ni_r[p]);
-        const uint64_t hw = w < hstride ? H[i * hstride + w] : 0ull;
-        a0 += ((hw >> lane) & 1ull) ? ps : -ps;
-        a1 += ((hw >> (32 + lane)) & 1ull) ? ps : -ps;
-      }
-      sums[j * (64 * W) + 64 * w + lane] += a0;
-      sums[j * (64 * W) + 64 * w + 32 + lane] += a1;
-    }
-  }
+// Hash values of Alg. 4: the kept sums plus the increment's sums, sums[x] += d[x]
+// (int64, exact).
+__global__ void k_add_i64(const int64_t *d, int64_t n, int64_t *sums) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
+    sums[x] += d[x];
 }
 
 // Per-user rating lists of the enlarged model: the old list and the user's
@@ -435,14 +415,22 @@ lshmf_status ingest(Handle *h, int64_t M_new, int64_t N_new, const int32_t *d_i,
   LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kus, n, uint64_t(Nt), Mt, nu_ptr);
   LSHMF_LAUNCH(h, k_ing_ptr, g, 256, 0, st, kis, n, uint64_t(Mt), Nt, ni_ptr);
   LSHMF_TRY(check_device_flag(h, st, "ingest (increment: index out of range, an old user-item pair, or a duplicate)"));
-  // hash values (Alg. 4): sums of the enlarged item set, then keys of all items
+  // hash values (Alg. 4): sums of the enlarged item set, then keys of all items.  The increment's own
+  // sums come from the signature kernel run over the increment's by-item lists (its item pointers,
+  // raters and ratings form a CSC over users [0, Mt)) and are added to the kept sums: Eq. 3's sums
+  // are linear in the raters, so old sums + increment sums = the sums of the enlarged rating set.
   int64_t *sums = B[0].as<int64_t>();
   LSHMF_CUDA(h, cudaMemcpyAsync(sums, S.sums.p, sizeof(int64_t) * 64 * W * N, cudaMemcpyDeviceToDevice, st));
   LSHMF_CUDA(h, cudaMemsetAsync(sums + 64 * W * N, 0, sizeof(int64_t) * 64 * W * (Nt - N), st));
   if (n > 0) {
-    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(Nt, 8), 16L * h->num_sms));
-    LSHMF_LAUNCH(h, k_ing_sums, gs, 256, 0, st, ni_ptr, ni_i, ni_r, Nt, d_H, (c.L * c.bits + 63) / 64, W,
-                 c.psi_pow, sums);
+    LSHMF_TRY(ensure(h, h->tmp[1], sizeof(int64_t) * 64 * W * Nt + 64, "ingest increment sums"));
+    LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * Nt + 16, "signatures"));
+    int64_t *dsum = h->tmp[1].as<int64_t>();
+    LSHMF_TRY(signature_sums(h, ni_ptr, ni_i, ni_r, n, Nt, Mt, d_H, W, dsum, h->tmp[0].as<uint32_t>(),
+                             "ingest (increment lists)", st));
+    const int64_t ns = 64 * int64_t(W) * Nt;
+    LSHMF_LAUNCH(h, k_add_i64, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ns, 256), 16L * h->num_sms)),
+                 256, 0, st, dsum, ns, sums);
   }
   // the handle now describes the enlarged model
   c.M = Mt;

@@ -321,8 +321,8 @@ lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, ui
 }
 
 template <int W, class ACC, class TAB>
-static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *r,
-                                   const uint64_t *H, const int64_t *unit_start, int64_t nunits,
+static lshmf_status run_signatures(Handle *h, int64_t N, const int64_t *col_ptr, const int32_t *row,
+                                   const uint8_t *r, const uint64_t *H, const int64_t *unit_start, int64_t nunits,
                                    const int64_t *split_idx, int64_t nsplit, uint32_t *sig, int64_t *sums,
                                    cudaStream_t st) {
   const lshmf_config &c = h->cfg;
@@ -331,25 +331,25 @@ static lshmf_status run_signatures(Handle *h, const int64_t *col_ptr, const int3
   ACC *acc = h->tmp[4].as<ACC>();
   LSHMF_CUDA(h, cudaMemsetAsync(acc, 0, accn * sizeof(ACC), st));
   LSHMF_LAUNCH(h, (k_sig_main<W, ACC, TAB>), (unsigned)ceil_div(nunits, SIG_WARPS), 32 * SIG_WARPS, 0, st,
-               col_ptr, row, r, H, (c.L * c.bits + 63) / 64, c.N, c.L, c.bits, c.psi_pow, unit_start, nunits,
+               col_ptr, row, r, H, (c.L * c.bits + 63) / 64, N, c.L, c.bits, c.psi_pow, unit_start, nunits,
                split_idx, acc, sig, sums);
   if (nsplit > 0)
-    LSHMF_LAUNCH(h, (k_sig_finalize<W, ACC>), (unsigned)ceil_div(c.N, 8), 256, 0, st, unit_start, split_idx,
-                 c.N, c.L, c.bits, acc, sig, sums);
+    LSHMF_LAUNCH(h, (k_sig_finalize<W, ACC>), (unsigned)ceil_div(N, 8), 256, 0, st, unit_start, split_idx,
+                 N, c.L, c.bits, acc, sig, sums);
   return LSHMF_OK;
 }
 
 template <class ACC, class TAB>
-static lshmf_status dispatch_sig(Handle *h, int W, const int64_t *col_ptr, const int32_t *row,
+static lshmf_status dispatch_sig(Handle *h, int W, int64_t N, const int64_t *col_ptr, const int32_t *row,
                                  const uint8_t *r, const uint64_t *H, const int64_t *us, int64_t nu,
                                  const int64_t *si, int64_t ns, uint32_t *sig, int64_t *sums, cudaStream_t st) {
   switch (W) {
-    case 1: return run_signatures<1, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 2: return run_signatures<2, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 3: return run_signatures<3, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 4: return run_signatures<4, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 8: return run_signatures<8, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
-    case 16: return run_signatures<16, ACC, TAB>(h, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 1: return run_signatures<1, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 2: return run_signatures<2, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 3: return run_signatures<3, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 4: return run_signatures<4, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 8: return run_signatures<8, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
+    case 16: return run_signatures<16, ACC, TAB>(h, N, col_ptr, row, r, H, us, nu, si, ns, sig, sums, st);
     default: return set_err(h, LSHMF_EINVAL, "internal: unsupported padded word count %d", W);
   }
 }
@@ -651,13 +651,16 @@ __global__ void k_set_i64_s(int64_t *p, int64_t v) { *p = v; }
 
 // Keys of Eq. (3) for all items into the handle's key buffer (tmp[0], L x N); the
 // pre-sign sums are kept for the online update.  *sig receives the buffer.
-lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,
-                              const uint64_t *H, uint32_t **sig_buf, cudaStream_t st) {
+// Padded 64-bit hash words per item of the kept sums (1-4, 8 or 16).
+static int padded_words(const lshmf_config &c) {
+  const int W = (c.L * c.bits + 63) / 64;
+  return W <= 4 ? W : (W <= 8 ? 8 : 16);
+}
+
+lshmf_status signature_sums(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,
+                            int64_t N, int64_t M, const uint64_t *H, int W, int64_t *sums, uint32_t *sig,
+                            const char *what, cudaStream_t st) {
   const lshmf_config &c = h->cfg;
-  const int64_t N = c.N;
-  const int nb = c.L * c.bits;
-  int W = (nb + 63) / 64;
-  if (W > 4) W = W <= 8 ? 8 : 16;
   // --- bounds: int32 sums are exact if rmax^p * maxcol < 2^31
   LSHMF_TRY(ensure(h, h->tmp[5], sizeof(int64_t) * (3 * (N + 1) + 8), "signature units"));
   int64_t *units = h->tmp[5].as<int64_t>();
@@ -667,8 +670,8 @@ lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *
   LSHMF_CUDA(h, cudaMemsetAsync(bounds, 0, 2 * sizeof(unsigned long long), st));
   LSHMF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
   const unsigned g = (unsigned)std::min<int64_t>(ceil_div(std::max(N, nnz), 256), 8L * h->num_sms);
-  LSHMF_LAUNCH(h, k_sig_bounds, g, 256, 0, st, col_ptr, N, row, rc, nnz, c.M, bounds, h->d_err);
-  LSHMF_TRY(check_device_flag(h, st, "build_neighbours (CSC input)"));
+  LSHMF_LAUNCH(h, k_sig_bounds, g, 256, 0, st, col_ptr, N, row, rc, nnz, M, bounds, h->d_err);
+  LSHMF_TRY(check_device_flag(h, st, what));
   LSHMF_LAUNCH(h, k_sig_units, g, 256, 0, st, col_ptr, N, units);
   LSHMF_TRY(exclusive_scan_i64(h, units, unit_start, N, st));
   LSHMF_LAUNCH(h, k_sig_split_flags, g, 256, 0, st, unit_start, N, units);
@@ -680,22 +683,29 @@ lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *
   for (int q = 0; q < c.psi_pow; ++q) psimax *= double(hb[1]);
   const double bound = psimax * 2.0 * double(std::max<int64_t>(1, hb[0]));
   const bool tab64 = 32.0 * psimax >= 4294967296.0;   // a batch of 32 Psi values overflows uint32
+  if (bound < 2147483647.0 && !tab64)
+    return dispatch_sig<int32_t, uint32_t>(h, W, N, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                           sums, st);
+  if (!tab64)
+    return dispatch_sig<int64_t, uint32_t>(h, W, N, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                           sums, st);
+  return dispatch_sig<int64_t, uint64_t>(h, W, N, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
+                                         sums, st);
+}
+
+lshmf_status signatures_stage(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,
+                              const uint64_t *H, uint32_t **sig_buf, cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  const int64_t N = c.N;
+  const int W = padded_words(c);
   // --- signatures into tmp sig buffer (L x N); the handle keeps the pre-sign sums
   // (N x 64W, int64) for the online update (Sec. 4.3)
   LSHMF_TRY(ensure(h, h->tmp[0], sizeof(uint32_t) * c.L * N + 16, "signatures"));
   uint32_t *sig = h->tmp[0].as<uint32_t>();
   h->lsh.ready = false;
   LSHMF_TRY(ensure(h, h->lsh.sums, sizeof(int64_t) * 64 * W * N, "kept signature sums"));
-  int64_t *sums = h->lsh.sums.as<int64_t>();
-  if (bound < 2147483647.0 && !tab64)
-    LSHMF_TRY((dispatch_sig<int32_t, uint32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
-                                               sums, st)));
-  else if (!tab64)
-    LSHMF_TRY((dispatch_sig<int64_t, uint32_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
-                                               sums, st)));
-  else
-    LSHMF_TRY((dispatch_sig<int64_t, uint64_t>(h, W, col_ptr, row, rc, H, unit_start, nunits, split_idx, nsplit, sig,
-                                               sums, st)));
+  LSHMF_TRY(signature_sums(h, col_ptr, row, rc, nnz, N, c.M, H, W, h->lsh.sums.as<int64_t>(), sig,
+                           "build_neighbours (CSC input)", st));
   h->lsh.W = W;
   h->lsh.N = N;
   h->lsh.ready = true;
