@@ -116,8 +116,13 @@ __global__ void k_sig_bounds(const int64_t *col_ptr, int64_t N, const int32_t *r
     mr = max(mr, (unsigned long long)r[p]);
     if (row[p] < 0 || row[p] >= M) atomicOr(err, DERR_INDEX);
   }
-  atomicMax(&out[0], mlen);
-  atomicMax(&out[1], mr);
+  // one atomic per warp (a column length is below 2^31, a rating below 2^8): thousands of threads
+  // hitting the same two words one by one would serialise in L2
+  const unsigned wl = __reduce_max_sync(0xffffffffu, unsigned(mlen)), wr = __reduce_max_sync(0xffffffffu, unsigned(mr));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)wl);
+    atomicMax(&out[1], (unsigned long long)wr);
+  }
 }
 
 template <class ACC>

@@ -57,7 +57,9 @@ __global__ void k_emit_A(const uint64_t *kA, const uint32_t *vA, const uint8_t *
     s += rv;
     if (p > 0 && kA[p - 1] == k) atomicOr(err, DERR_DUP);
   }
-  atomicAdd(rsum, s);
+  // one atomic per warp (exact: integer sum)
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(rsum, s);
 }
 
 __global__ void k_keys_block(const int32_t *iA, const int32_t *jA, int64_t nnz, int64_t M, int64_t N, int P,
@@ -181,7 +183,9 @@ __global__ void k_max_diff(const int64_t *ptr, int64_t G, unsigned long long *ou
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < G;
        g += int64_t(gridDim.x) * blockDim.x)
     m = max(m, (unsigned long long)(ptr[g + 1] - ptr[g]));
-  atomicMax(out, m);
+  // one atomic per warp: a million threads on one word would serialise in L2
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // --------------------------------------------- explicit-neighbour index ----
