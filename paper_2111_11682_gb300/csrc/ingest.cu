@@ -239,9 +239,8 @@ __global__ void k_ing_nbr_pre(const IngArgs a) {
   }
 }
 
-// Item update of Alg. 4: one warp per new item; users fixed.  The rater's data of
-// the next rating is loaded while the current one runs (it does not depend on
-// the item chain).
+// Item update of Alg. 4: one warp per new item; users fixed; two ratings per step
+// (their errors from one warp reduction, see below).
 template <int FPL, int KPL>
 __global__ void k_ing_items(const IngArgs a) {
   const int lane = threadIdx.x & 31, F = a.F, K = a.K;
@@ -264,67 +263,111 @@ __global__ void k_ing_items(const IngArgs a) {
     for (int kk = 0; kk < KPL; ++kk) nV += __popc(__ballot_sync(0xffffffffu, lane + 32 * kk < K));
     float bhj = a.bh[j];
     const int64_t p0 = a.ni_ptr[j], p1 = a.ni_ptr[j + 1];
-    // operands of rating p: rater's u, b; mask; neighbour ratings; the rating
-    float un[FPL], bn = 0.f, rn = 0.f;
-    uint32_t mn[KPL];
-    uint8_t xn[KPL];
-    auto load = [&](int64_t p) {
+    // operands of a rating: rater's u, b; mask; neighbour ratings; the rating.  Two ratings are run
+    // per step (below); the operands of the next two are loaded while the current two run (they do
+    // not depend on the item chain).
+    struct Op {
+      float u[FPL], b, r;
+      uint32_t m[KPL];
+      uint8_t x[KPL];
+    };
+    auto load = [&](int64_t p, Op &o) {
       const int64_t i = a.ni_i[p];
-      bn = a.b[i];
-      rn = float(a.ni_r[p]) * a.inv_scale;
+      o.b = a.b[i];
+      o.r = float(a.ni_r[p]) * a.inv_scale;
 #pragma unroll
-      for (int f = 0; f < FPL; ++f) un[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
+      for (int f = 0; f < FPL; ++f) o.u[f] = lane * FPL + f < F ? a.U[i * F + lane * FPL + f] : 0.f;
 #pragma unroll
       for (int kk = 0; kk < KPL; ++kk) {
         const int k = lane + 32 * kk;
-        mn[kk] = a.xm[2 * p + kk];
-        xn[kk] = k < K ? a.xr[p * K + k] : 0;
+        o.m[kk] = a.xm[2 * p + kk];
+        o.x[kk] = k < K ? a.xr[p * K + k] : 0;
       }
     };
-    if (p0 < p1) load(p0);
-    for (int64_t p = p0; p < p1; ++p) {
-      float u[FPL];
-      uint32_t mk[KPL];
-      uint8_t xb[KPL];
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) u[f] = un[f];
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        mk[kk] = mn[kk];
-        xb[kk] = xn[kk];
-      }
-      const float bi = bn, r = rn;
-      if (p + 1 < p1) load(p + 1);
-      float xk[KPL];
-      bool exk[KPL];
-      float sxw = 0.f, sc = 0.f, dot = 0.f;
-      int nR = 0;
-#pragma unroll
-      for (int kk = 0; kk < KPL; ++kk) {
-        const bool valid = lane + 32 * kk < K;
-        const bool ex = (mk[kk] >> lane) & 1u;
-        const float x = ex ? float(xb[kk]) * a.inv_scale - (a.mu + bi + bq[kk]) : 0.f;
-        xk[kk] = x;
-        exk[kk] = ex;
-        sxw = fmaf(x, w[kk], sxw);
-        sc += (valid && !ex) ? c[kk] : 0.f;
-        nR += __popc(mk[kk]);
-      }
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) dot = fmaf(u[f], v[f], dot);
-      warp_sum3(sxw, sc, dot);
-      const int nN = nV - nR;
-      const float sR = nR > 0 ? rsqrtf(float(nR)) : 0.f, sN = nN > 0 ? rsqrtf(float(nN)) : 0.f;
-      const float rhat = a.mu + bi + bhj + sxw * sR + sc * sN + dot;
-      const float e = r - rhat;
-      bhj = bhj + g_bh * (e - l_bh * bhj);
-#pragma unroll
-      for (int f = 0; f < FPL; ++f) v[f] = v[f] + g_v * (e * u[f] - l_v * v[f]);
+    const float q_bh = 1.f - g_bh * l_bh, q_v = 1.f - g_v * l_v, q_w = 1.f - g_w * l_w, q_c = 1.f - g_c * l_c;
+    Op n0, n1;
+    if (p0 < p1) load(p0, n0);
+    if (p0 + 1 < p1) load(p0 + 1, n1);
+    for (int64_t p = p0; p < p1; p += 2) {
+      // Two consecutive ratings t = 0, 1 of the item.  Every item-side update of Eq. 5 is linear in
+      // the error, so with the state s before rating 0, rating 1's prediction after rating 0's
+      // updates is base1 + L10 e0: base1 is Eq. 1 on the state decayed by rating 0's steps
+      // (q = 1 - gamma lambda on bhat, v, and on w_k / c_k for k in R_0 / N_0), and
+      // L10 = g_bh + g_v u1.u0 + g_w sR1 sR0 sum_{k in R1 and R0} x1k x0k + g_c sN1 sN0 |N1 and N0|.
+      // So e0 and e1 come from one warp reduction; then the two steps of Eq. 5 run in order.
+      const Op o0 = n0, o1 = n1;
+      const bool two = p + 1 < p1;
+      if (p + 2 < p1) load(p + 2, n0);
+      if (p + 3 < p1) load(p + 3, n1);
+      float xk0[KPL], xk1[KPL];
+      bool ex0[KPL], ex1[KPL];
+      float sxw0 = 0.f, sc0 = 0.f, dot0 = 0.f, sxw1 = 0.f, sc1 = 0.f, dot1 = 0.f, uu = 0.f, xx = 0.f;
+      int nR0 = 0, nR1 = 0, nn = 0;
 #pragma unroll
       for (int kk = 0; kk < KPL; ++kk) {
         const bool valid = lane + 32 * kk < K;
-        if (exk[kk]) w[kk] = w[kk] + g_w * (sR * e * xk[kk] - l_w * w[kk]);
-        else if (valid) c[kk] = c[kk] + g_c * (sN * e - l_c * c[kk]);
+        ex0[kk] = (o0.m[kk] >> lane) & 1u;
+        ex1[kk] = two && ((o1.m[kk] >> lane) & 1u);
+        xk0[kk] = ex0[kk] ? float(o0.x[kk]) * a.inv_scale - (a.mu + o0.b + bq[kk]) : 0.f;
+        xk1[kk] = ex1[kk] ? float(o1.x[kk]) * a.inv_scale - (a.mu + o1.b + bq[kk]) : 0.f;
+        sxw0 = fmaf(xk0[kk], w[kk], sxw0);
+        sc0 += (valid && !ex0[kk]) ? c[kk] : 0.f;
+        const float w1 = ex0[kk] ? q_w * w[kk] : w[kk];
+        const float c1 = (valid && !ex0[kk]) ? q_c * c[kk] : c[kk];
+        sxw1 = fmaf(xk1[kk], w1, sxw1);
+        sc1 += (valid && !ex1[kk]) ? c1 : 0.f;
+        xx = fmaf(xk1[kk], xk0[kk], xx);
+        nR0 += __popc(o0.m[kk]);
+        nR1 += two ? __popc(o1.m[kk]) : 0;
+        nn += __popc(__ballot_sync(0xffffffffu, valid && !ex0[kk] && !ex1[kk]));
+      }
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) {
+        dot0 = fmaf(o0.u[f], v[f], dot0);
+        dot1 = fmaf(o1.u[f], v[f], dot1);
+        uu = fmaf(o1.u[f], o0.u[f], uu);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sxw0 += __shfl_xor_sync(0xffffffffu, sxw0, o);
+        sc0 += __shfl_xor_sync(0xffffffffu, sc0, o);
+        dot0 += __shfl_xor_sync(0xffffffffu, dot0, o);
+        sxw1 += __shfl_xor_sync(0xffffffffu, sxw1, o);
+        sc1 += __shfl_xor_sync(0xffffffffu, sc1, o);
+        dot1 += __shfl_xor_sync(0xffffffffu, dot1, o);
+        uu += __shfl_xor_sync(0xffffffffu, uu, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+      }
+      const int nN0 = nV - nR0, nN1 = nV - nR1;
+      const float sR0 = nR0 > 0 ? rsqrtf(float(nR0)) : 0.f, sN0 = nN0 > 0 ? rsqrtf(float(nN0)) : 0.f;
+      const float sR1 = nR1 > 0 ? rsqrtf(float(nR1)) : 0.f, sN1 = nN1 > 0 ? rsqrtf(float(nN1)) : 0.f;
+      const float e0 = o0.r - (a.mu + o0.b + bhj + sxw0 * sR0 + sc0 * sN0 + dot0);
+      float e1 = 0.f;
+      if (two) {
+        const float base1 = a.mu + o1.b + q_bh * bhj + sxw1 * sR1 + sc1 * sN1 + q_v * dot1;
+        const float l10 = g_bh + g_v * uu + g_w * sR1 * sR0 * xx + g_c * sN1 * sN0 * float(nn);
+        e1 = o1.r - base1 - l10 * e0;
+      }
+      // the two steps of Eq. 5, in order
+      bhj = bhj + g_bh * (e0 - l_bh * bhj);
+#pragma unroll
+      for (int f = 0; f < FPL; ++f) v[f] = v[f] + g_v * (e0 * o0.u[f] - l_v * v[f]);
+#pragma unroll
+      for (int kk = 0; kk < KPL; ++kk) {
+        const bool valid = lane + 32 * kk < K;
+        if (ex0[kk]) w[kk] = w[kk] + g_w * (sR0 * e0 * xk0[kk] - l_w * w[kk]);
+        else if (valid) c[kk] = c[kk] + g_c * (sN0 * e0 - l_c * c[kk]);
+      }
+      if (two) {
+        bhj = bhj + g_bh * (e1 - l_bh * bhj);
+#pragma unroll
+        for (int f = 0; f < FPL; ++f) v[f] = v[f] + g_v * (e1 * o1.u[f] - l_v * v[f]);
+#pragma unroll
+        for (int kk = 0; kk < KPL; ++kk) {
+          const bool valid = lane + 32 * kk < K;
+          if (ex1[kk]) w[kk] = w[kk] + g_w * (sR1 * e1 * xk1[kk] - l_w * w[kk]);
+          else if (valid) c[kk] = c[kk] + g_c * (sN1 * e1 - l_c * c[kk]);
+        }
       }
     }
 #pragma unroll
