@@ -275,14 +275,28 @@ __global__ void k_radix_hist(const uint64_t *keys, int64_t n, int shift, int64_t
   hist[int64_t(threadIdx.x) * ntiles + blockIdx.x] = hs[threadIdx.x];
 }
 
+// Dynamic shared memory of k_radix_scatter: the tile's keys and values in digit order, the per-warp
+// digit counts, the tile's digit starts and the digits' global starts.
+constexpr size_t RS_SMEM = size_t(RS_TILE) * (sizeof(uint64_t) + sizeof(uint32_t)) +
+                           sizeof(uint32_t) * RS_WARPS * 256 + sizeof(uint32_t) * 256 + sizeof(int64_t) * 256;
+
+// One pass of the stable LSD sort: each tile ranks its elements by digit (per warp with match_any,
+// in index order), places them in shared memory in (digit, index) order, then writes each digit's
+// run to its global position with consecutive threads on consecutive addresses.
 __global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout,
                                 uint32_t *vout, int64_t n, int shift, int64_t ntiles,
                                 const int64_t *offs) {
-  __shared__ uint32_t wcnt[RS_WARPS][256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);
+  uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
+  uint32_t(*wcnt)[256] = reinterpret_cast<uint32_t(*)[256]>(sv + RS_TILE);
+  uint32_t *ls = &wcnt[RS_WARPS - 1][0] + 256;          // tile-local start of each digit
+  int64_t *goff = reinterpret_cast<int64_t *>(ls + 256);  // global start of each digit's run of this tile
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < RS_WARPS * 256; e += RS_T) (&wcnt[0][0])[e] = 0;
   __syncthreads();
-  const int64_t base = int64_t(blockIdx.x) * RS_TILE + int64_t(w) * (RS_PER * 32);
+  const int64_t tile0 = int64_t(blockIdx.x) * RS_TILE;
+  const int64_t base = tile0 + int64_t(w) * (RS_PER * 32);
   uint64_t k[RS_PER];
   uint32_t v[RS_PER];
   uint32_t loc[RS_PER];
@@ -306,13 +320,37 @@ __global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64
   }
   __syncthreads();
   {
+    // per digit: warps' starts inside the digit's run, the run's length, its global start
     const int d = threadIdx.x;  // RS_T == 256 digits
-    uint32_t run = (uint32_t)offs[int64_t(d) * ntiles + blockIdx.x];
+    uint32_t run = 0;
 #pragma unroll
     for (int q = 0; q < RS_WARPS; ++q) {
-      uint32_t c = wcnt[q][d];
+      const uint32_t c = wcnt[q][d];
       wcnt[q][d] = run;
       run += c;
+    }
+    ls[d] = run;
+    goff[d] = offs[int64_t(d) * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {   // exclusive scan of the 256 run lengths (8 per lane)
+    uint32_t c[8], t = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      c[q] = ls[lane * 8 + q];
+      t += c[q];
+    }
+    uint32_t incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - t;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ls[lane * 8 + q] = run;
+      run += c[q];
     }
   }
   __syncthreads();
@@ -320,11 +358,20 @@ __global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64
   for (int r = 0; r < RS_PER; ++r) {
     int64_t x = base + r * 32 + lane;
     if (x < n) {
-      unsigned d = (k[r] >> shift) & 255u;
-      uint32_t pos = wcnt[w][d] + loc[r];
-      kout[pos] = k[r];
-      vout[pos] = v[r];
+      const unsigned d = (k[r] >> shift) & 255u;
+      const uint32_t lp = ls[d] + wcnt[w][d] + loc[r];
+      sk[lp] = k[r];
+      sv[lp] = v[r];
     }
+  }
+  __syncthreads();
+  const int tn = int(n - tile0 < int64_t(RS_TILE) ? n - tile0 : int64_t(RS_TILE));
+  for (int e = threadIdx.x; e < tn; e += RS_T) {
+    const uint64_t key = sk[e];
+    const unsigned d = (key >> shift) & 255u;
+    const int64_t pos = goff[d] + (e - int(ls[d]));
+    kout[pos] = key;
+    vout[pos] = sv[e];
   }
 }
 
@@ -348,6 +395,7 @@ lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, u
   LSHMF_TRY(ensure(h, h->tmp[6], nh * (sizeof(uint32_t) + sizeof(int64_t)) + 64, "radix histogram"));
   uint32_t *hist = h->tmp[6].as<uint32_t>();
   int64_t *offs = reinterpret_cast<int64_t *>(h->tmp[6].as<char>() + ((nh * sizeof(uint32_t) + 15) & ~size_t(15)));
+  LSHMF_CUDA(h, cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM));
   const int passes = (nbits + 7) / 8;
   uint64_t *ka = keys_in, *kb = keys_out;
   uint32_t *va = vals_in, *vb = vals_out;
@@ -362,7 +410,7 @@ lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, u
     LSHMF_LAUNCH(h, k_u32_to_i64, (unsigned)std::min<int64_t>(ceil_div(nh, 256), 4096), 256, 0, st, hist,
                  offs, nh);
     LSHMF_TRY(exclusive_scan_i64(h, offs, offs, nh, st));
-    LSHMF_LAUNCH(h, k_radix_scatter, (unsigned)ntiles, RS_T, 0, st, ka, va, kb, vb, n, shift, ntiles, offs);
+    LSHMF_LAUNCH(h, k_radix_scatter, (unsigned)ntiles, RS_T, RS_SMEM, st, ka, va, kb, vb, n, shift, ntiles, offs);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
