@@ -866,18 +866,21 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         job_e2e()
+        clk_e2e = Clocks(local_rank)
         barrier()
+        clk_e2e.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
             rmse_e2e = job_e2e()
         e1.record(stream)
         barrier()
+        clocks_e2e = clk_e2e.stop()
         ms_e2e = e0.elapsed_time(e1) / args.steps
         ms_e2e = max_over_ranks(ms_e2e, world, dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         e2e = {"value": replica_throughput(E * nnz, world, ms_e2e), "unit": "rating-updates/s", "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8, "clocks": clocks_e2e}
 
     signatures = topn = None
     if rank == 0:
