@@ -224,6 +224,7 @@ k_index(const int64_t *user_ptr, const int32_t *csr_j, const uint8_t *csr_r, con
     for (int64_t c = c0 + w; c < c1; c += nw) {
       const int32_t j = csr_j[c];
       const int64_t b = bposC[c];
+      if (MODE == 1 && cnt[b] == 0) continue;   // no explicit neighbour: nothing to pack (warp-uniform)
       uint32_t m[2] = {0, 0};
       int val[2] = {0, 0};
 #pragma unroll
