@@ -507,8 +507,10 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
     Times E epochs of every instance (CUDA events around the whole job, parameters reset untimed):
     per-instance lshmf_train_epoch calls from a host loop (one run), against one CUDA graph of the
     whole job (lshmf_batch) with instances on parallel branches, round-robin or longest-first by the
-    autotuner's epoch time (median of 3 after one warm-up).  sm_time_bound_ms = E x the sum over
-    instances of epoch ms x min(P, SMs) / SMs, the least time the SMs allow."""
+    autotuner's epoch time, and against one launch of the epoch kernel per epoch for all instances
+    (lshmf_batch_create_fused), each median of 3 after one warm-up.  sm_time_bound_ms = E x the sum
+    over instances of epoch ms x min(P, SMs) / SMs: the least time the SMs allow when each instance's
+    epoch holds min(P, SMs) SMs for its own duration (a fused launch is not held to it)."""
     import dataclasses
 
     import torch
@@ -607,6 +609,16 @@ def measure_batch(dev, n_inst=256, E=3, seed=7):
         out["modes"][name] = {"ms": round(ms, 2), "rating_updates_per_s": total / (ms / 1e3),
                               "kernels": b.kernels, "equal_to_per_instance": bool(same)}
         b.close()
+    # one launch of the epoch kernel per epoch for all instances (lshmf_batch_create_fused)
+    b = Batch(models, ps, epoch0=0, epochs=E, fused=True)
+    timed(b.run, reps=1)
+    ms = timed(b.run)
+    b.check()
+    same = all(torch.equal(getattr(q, n), getattr(r, n)) for q, r in zip(ps, ref) for n in ("U", "V", "W"))
+    out["modes"]["fused_one_epoch_launch_for_all_instances"] = {
+        "ms": round(ms, 2), "rating_updates_per_s": total / (ms / 1e3), "kernels": b.kernels,
+        "equal_to_per_instance": bool(same)}
+    b.close()
     for m in models:
         m.close()
     return out

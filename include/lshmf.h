@@ -397,6 +397,21 @@ typedef struct lshmf_batch lshmf_batch;
 lshmf_status lshmf_batch_create(lshmf_handle *const *handles, const lshmf_params *params, const double *cost,
                                 int32_t n, int32_t epoch0, int32_t epochs, int32_t branches, lshmf_batch **out);
 
+/* The same batch with one launch of the epoch kernel per epoch for ALL
+ * instances (plus one prologue kernel per epoch that zeroes every instance's
+ * block counter and flags and takes its bhat snapshots): CTA b of the launch
+ * runs instance cta[b] (min(P, SMs) CTAs per instance, largest instances
+ * first) exactly as that instance's own epoch launch would, so the result is
+ * bit-identical to separate lshmf_train_epoch calls.  Requirements: every
+ * handle prepared, the same ceil(F/32) and ceil(K/32) for all instances (one
+ * kernel instantiation), the same device; else EINVAL.  The handles' SGD slot
+ * options are honoured; the groups per CTA are the smallest any instance
+ * asks for.  The arguments of every epoch are built here (device memory
+ * owned by the batch), so the parameter arrays and prepared layouts must not
+ * move while the batch lives.  Run, check, kernels and destroy as above. */
+lshmf_status lshmf_batch_create_fused(lshmf_handle *const *handles, const lshmf_params *params, int32_t n,
+                                      int32_t epoch0, int32_t epochs, lshmf_batch **out);
+
 /* The assignment lshmf_batch_create uses (host only, no GPU needed):
  * branch_of[x] = branch of instance x, order = instances in capture order,
  * for min(branches, n) branches.  cost NULL: round-robin in index order;

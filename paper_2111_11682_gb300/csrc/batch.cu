@@ -6,11 +6,17 @@
 // every epoch of the job, instances spread over parallel branches (fork from
 // one event, join into the origin stream): round-robin, or longest-first by a
 // cost the caller gives (each instance, largest first, to the least-loaded
-// branch), so that uneven instances end together.  The stratum kernel's
-// waits are all inside one CTA (block slots and chunk rings live in shared
-// memory), so kernels of different instances may share the GPU in any mix.
-// Replaying the graph costs one launch call for the whole job, and small
-// instances, whose strata use only min(P, SMs) CTAs, fill the GPU together.
+// branch), so that uneven instances end together.  The epoch kernel's CTAs
+// wait only on blocks that running CTAs of their own launch have taken, so
+// kernels of different instances may share the GPU in any mix.  Replaying the
+// graph costs one launch call for the whole job, and small instances, whose
+// epochs use only min(P, SMs) CTAs, fill the GPU together.
+//
+// lshmf_batch_create_fused records instead, per epoch, one prologue kernel and
+// ONE launch of the epoch kernel for every instance together (CTA b runs
+// instance cta_inst[b], largest instances first), so the SMs that one
+// instance's CTAs leave idle are taken by other instances' CTAs inside the
+// same launch.
 #include <algorithm>
 #include <vector>
 
@@ -26,6 +32,7 @@ struct lshmf_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<lshmf::Handle *> hs;
   int64_t kernels = 0;
+  lshmf::FusedEpochs *fused = nullptr;   // device state of a fused batch
 };
 
 using lshmf::Handle;
@@ -36,6 +43,10 @@ void free_batch(lshmf_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->fused) {
+    cudaDeviceSynchronize();   // a replay in flight may still read the fused arguments
+    lshmf::fused_free(b->fused);
+  }
   delete b;
 }
 
@@ -150,6 +161,53 @@ lshmf_status lshmf_batch_create(lshmf_handle *const *handles, const lshmf_params
     if (t) cudaStreamDestroy(t);
   cudaStreamDestroy(origin);
   cudaGetLastError();   // a failed capture leaves no sticky error behind for the caller's next call
+  if (s != LSHMF_OK) {
+    free_batch(b);
+    return s;
+  }
+  *out = b;
+  return LSHMF_OK;
+}
+
+lshmf_status lshmf_batch_create_fused(lshmf_handle *const *handles, const lshmf_params *params, int32_t n,
+                                      int32_t epoch0, int32_t epochs, lshmf_batch **out) {
+  if (!out) return LSHMF_EINVAL;
+  *out = nullptr;
+  if (!handles || !params || n < 1 || epoch0 < 0 || epochs < 1) return LSHMF_EINVAL;
+  for (int32_t x = 0; x < n; ++x) {
+    if (!handles[x]) return LSHMF_EINVAL;
+    for (int32_t y = 0; y < x; ++y)
+      if (handles[y] == handles[x]) return lshmf::set_err(&handles[x]->h, LSHMF_EINVAL, "batch: handle listed twice");
+  }
+  lshmf_batch *b = new lshmf_batch();
+  for (int32_t x = 0; x < n; ++x) b->hs.push_back(&handles[x]->h);
+  lshmf_status s = lshmf::fused_setup(b->hs.data(), params, n, epoch0, epochs, &b->fused);
+  if (s != LSHMF_OK) {
+    free_batch(b);
+    return s;
+  }
+  cudaStream_t origin = nullptr;
+  if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess) {
+    free_batch(b);
+    return LSHMF_ECUDA;
+  }
+  if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    s = LSHMF_ECUDA;
+  } else {
+    for (int32_t e = 0; e < epochs && s == LSHMF_OK; ++e) s = lshmf::fused_launch(b->fused, e, origin);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(origin, &g);
+    if (ee != cudaSuccess && s == LSHMF_OK) s = LSHMF_ECUDA;
+    if (s == LSHMF_OK && g) {
+      b->graph = g;
+      if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) s = LSHMF_ECUDA;
+      b->kernels = count_kernels(g);
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaStreamDestroy(origin);
+  cudaGetLastError();
   if (s != LSHMF_OK) {
     free_batch(b);
     return s;

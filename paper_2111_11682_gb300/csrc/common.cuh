@@ -193,6 +193,16 @@ lshmf_status radix_sort_pairs(Handle *h, uint64_t *keys_in, uint32_t *vals_in, u
 lshmf_status topk_from_sig(Handle *h, const uint32_t *sig, int64_t N, int32_t *nbr, cudaStream_t st);
 // Keys (L x N) from pre-sign sums (N x 64W).
 lshmf_status keys_from_sums(Handle *h, const int64_t *sums, int W, int64_t N, uint32_t *sig, cudaStream_t st);
+// Batched training with one launch of the epoch kernel per epoch for all instances (sgd.cu):
+// fused_setup builds every instance's kernel arguments for epochs [epoch0, epoch0 + epochs) and the
+// CTA-to-instance table (device memory owned by the result); fused_launch enqueues epoch
+// epoch0 + e of every instance (a prologue kernel and the epoch kernel).
+struct FusedEpochs;
+lshmf_status fused_setup(Handle *const *hs, const lshmf_params *params, int32_t n, int32_t epoch0, int32_t epochs,
+                         FusedEpochs **out);
+lshmf_status fused_launch(FusedEpochs *f, int32_t e, cudaStream_t st);
+void fused_free(FusedEpochs *f);
+
 // Eq. 3 pre-sign sums (N x 64W, int64) and keys (L x N) of the N columns of a
 // CSC over users [0, M); `what` names the caller in a bad-input error.
 lshmf_status signature_sums(Handle *h, const int64_t *col_ptr, const int32_t *row, const uint8_t *rc, int64_t nnz,

@@ -61,6 +61,8 @@
 // flag, waits for its own copies in flight and returns.
 #include <cuda/atomic>
 
+#include <vector>
+
 #include <algorithm>
 #include <cstddef>
 
@@ -880,9 +882,10 @@ __device__ void consumer(const SgdArgs &a, const Smem &sm, Group<FPL, KPL> &G) {
   }
 }
 
+// The work of one CTA of an epoch launch: carve shared memory, then the
+// scheduler, consumer and producer warps.
 template <int FPL, int KPL>
-__global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
-k_sgd_epoch(const SgdArgs a, int ngroups) {
+__device__ __forceinline__ void sgd_cta(const SgdArgs &a, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
   // carve shared memory: [groups][ctl][qt][users][cnt]
@@ -923,6 +926,27 @@ k_sgd_epoch(const SgdArgs a, int ngroups) {
   }
 }
 
+template <int FPL, int KPL>
+__global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
+k_sgd_epoch(const SgdArgs a, int ngroups) {
+  sgd_cta<FPL, KPL>(a, ngroups);
+}
+
+// One launch for an epoch of many instances (batched training): CTA b runs
+// instance cta_inst[b] with that instance's arguments (copied to shared
+// memory), exactly as that instance's own epoch launch would.  An instance's
+// blocks are taken from its own counter only by running CTAs and wait only on
+// blocks taken before them, so every instance progresses whatever share of
+// its CTAs is resident.
+template <int FPL, int KPL>
+__global__ void __launch_bounds__(32 * (MAX_GROUPS * (GP + 1) + 1), 1)
+k_sgd_fused(const SgdArgs *args, const int32_t *cta_inst, int ngroups) {
+  __shared__ SgdArgs sa;
+  if (threadIdx.x == 0) sa = args[cta_inst[blockIdx.x]];
+  __syncthreads();
+  sgd_cta<FPL, KPL>(sa, ngroups);
+}
+
 __global__ void k_gather_bh0n(const float *bh0, const int32_t *nbr, int64_t n, float *bh0n) {
   for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
     bh0n[x] = bh0[nbr[x]];
@@ -942,21 +966,34 @@ __global__ void k_sum_seg_sq(const double *x, int64_t n, double *out) {
   if (threadIdx.x == 0) *out = sm[0];
 }
 
+// Dynamic shared memory of an epoch CTA: ng groups, ns block slots of maxu users.
 template <int FPL, int KPL>
-static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
-  // groups and block slots: as asked, else as many groups as fit and SGD_DEFAULT_SLOTS slots
-  const size_t gsz = sizeof(Group<FPL, KPL>);
-  auto need = [&](int ng, int ns) {
-    return gsz * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) + 2 * sizeof(int) * size_t(ns) * a.maxu;
-  };
+static size_t sgd_smem(int ng, int ns, int maxu) {
+  return sizeof(Group<FPL, KPL>) * ng + sizeof(CtaCtl) + sizeof(float) * 8 * (CH + 1) +
+         2 * sizeof(int) * size_t(ns) * maxu;
+}
+
+// Groups and block slots of a handle's epoch CTAs (as asked, else as many groups as fit and
+// SGD_DEFAULT_SLOTS slots) within `cap` bytes of shared memory.
+template <int FPL, int KPL>
+static lshmf_status sgd_tile(Handle *h, int maxu, size_t cap, int *ng_out, int *ns_out) {
   int ng = h->sgd_groups > 0 ? std::min(h->sgd_groups, MAX_GROUPS) : MAX_GROUPS;
   int ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : SGD_DEFAULT_SLOTS;
-  while (ng > 1 && need(ng, 1) > size_t(h->smem_optin)) --ng;
-  while (ns > 1 && need(ng, ns) > size_t(h->smem_optin)) --ns;
-  if (need(ng, ns) > size_t(h->smem_optin))
-    return set_err(h, LSHMF_EINVAL, "train: %d users in one block exceed shared memory; raise P", a.maxu);
+  while (ng > 1 && sgd_smem<FPL, KPL>(ng, 1, maxu) > cap) --ng;
+  while (ns > 1 && sgd_smem<FPL, KPL>(ng, ns, maxu) > cap) --ns;
+  if (sgd_smem<FPL, KPL>(ng, ns, maxu) > cap)
+    return set_err(h, LSHMF_EINVAL, "train: %d users in one block exceed shared memory; raise P", maxu);
+  *ng_out = ng;
+  *ns_out = ns;
+  return LSHMF_OK;
+}
+
+template <int FPL, int KPL>
+static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream_t st) {
+  int ng = 1, ns = 1;
+  LSHMF_TRY((sgd_tile<FPL, KPL>(h, a.maxu, size_t(h->smem_optin), &ng, &ns)));
   a.nslots = ns;
-  const size_t smem = need(ng, ns);
+  const size_t smem = sgd_smem<FPL, KPL>(ng, ns, a.maxu);
   // the attribute is a per-kernel cap shared by every handle: set it to the device maximum so that
   // launches of handles with different block sizes (captured together into one graph, or issued from
   // several threads) never see another handle's smaller cap
@@ -968,24 +1005,14 @@ static lshmf_status launch_strata(Handle *h, SgdArgs a, int n_strata, cudaStream
   return LSHMF_OK;
 }
 
-lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
-                          cudaStream_t st) {
+// The epoch kernel's arguments for a prepared handle, parameters p and epoch (learning rates of Eq. 7).
+static lshmf_status sgd_args(Handle *h, const lshmf_params *p, int32_t epoch, bool want_sq, SgdArgs &a) {
   const lshmf_config &c = h->cfg;
   TrainLayout &tl = h->tl;
   if (!tl.ready) return set_err(h, LSHMF_ESTATE, "train: lshmf_prepare_training has not succeeded");
   if (!p || !p->U || !p->V || !p->b || !p->bh || !p->W || !p->C)
     return set_err(h, LSHMF_EINVAL, "train: null parameter pointer");
   if (epoch < 0) return set_err(h, LSHMF_EINVAL, "train: epoch must be >= 0");
-  n_strata = std::min<int32_t>(std::max<int32_t>(n_strata, 0), c.P);
-  // epoch-start snapshot of bhat and of each item's neighbours' bhat (term (2) baselines)
-  LSHMF_CUDA(h, cudaMemcpyAsync(tl.bh0.p, p->bh, c.N * 4, cudaMemcpyDeviceToDevice, st));
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.N * c.K, 256), 16L * h->num_sms));
-  LSHMF_LAUNCH(h, k_gather_bh0n, g, 256, 0, st, tl.bh0.as<float>(), tl.nbr.as<int32_t>(), c.N * c.K,
-               tl.bh0n.as<float>());
-  // the epoch's block counter and per-block finished flags start at zero
-  LSHMF_CUDA(h, cudaMemsetAsync(tl.df.p, 0, sgd_flags_bytes(c.P), st));
-  if (h_sq) LSHMF_CUDA(h, cudaMemsetAsync(tl.seg_sq.p, 0, tl.nseg * 8, st));
-  SgdArgs a;
   a.sr = tl.sr.as<uint32_t>();
   a.rat = tl.rat.as<uint8_t>();
   a.mask = tl.mask.as<uint32_t>();
@@ -1023,11 +1050,30 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
   }
   a.F = c.F; a.K = c.K; a.P = c.P; a.mw = tl.mask_words; a.maxu = std::max(1, tl.max_users_per_block);
   a.nslots = 1;
-  a.want_sq = h_sq != nullptr;
+  a.n_strata = c.P;
+  a.want_sq = want_sq;
   a.polls = h->wait_polls > 0 ? h->wait_polls : SGD_DEFAULT_POLLS;
   a.tries = std::max<int64_t>(1, a.polls >> 2);
   a.withhold = h->test_withhold;
   a.err = h->d_err;
+  return LSHMF_OK;
+}
+
+lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32_t n_strata, double *h_sq,
+                          cudaStream_t st) {
+  const lshmf_config &c = h->cfg;
+  TrainLayout &tl = h->tl;
+  SgdArgs a;
+  LSHMF_TRY(sgd_args(h, p, epoch, h_sq != nullptr, a));
+  n_strata = std::min<int32_t>(std::max<int32_t>(n_strata, 0), c.P);
+  // epoch-start snapshot of bhat and of each item's neighbours' bhat (term (2) baselines)
+  LSHMF_CUDA(h, cudaMemcpyAsync(tl.bh0.p, p->bh, c.N * 4, cudaMemcpyDeviceToDevice, st));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.N * c.K, 256), 16L * h->num_sms));
+  LSHMF_LAUNCH(h, k_gather_bh0n, g, 256, 0, st, tl.bh0.as<float>(), tl.nbr.as<int32_t>(), c.N * c.K,
+               tl.bh0n.as<float>());
+  // the epoch's block counter and per-block finished flags start at zero
+  LSHMF_CUDA(h, cudaMemsetAsync(tl.df.p, 0, sgd_flags_bytes(c.P), st));
+  if (h_sq) LSHMF_CUDA(h, cudaMemsetAsync(tl.seg_sq.p, 0, tl.nseg * 8, st));
   const int fpl = (c.F + 31) / 32, kpl = (c.K + 31) / 32;
   lshmf_status s;
   if (fpl <= 1) s = kpl <= 1 ? launch_strata<1, 1>(h, a, n_strata, st) : launch_strata<1, 2>(h, a, n_strata, st);
@@ -1041,6 +1087,158 @@ lshmf_status train_strata(Handle *h, const lshmf_params *p, int32_t epoch, int32
     LSHMF_TRY(check_device_flag(h, st, "train"));
   }
   return LSHMF_OK;
+}
+
+
+// ------------------------------------------------- batched, one launch per epoch ----
+// Epoch-start state of one instance, set by the prologue kernel of a fused epoch: the scheduler's
+// counter and flags zeroed, the bhat snapshot and each item's neighbours' bhat (as train_strata).
+struct PrologueItem {
+  int32_t *df;
+  int64_t df_n;
+  const float *bh;
+  float *bh0;
+  int64_t N;
+  const int32_t *nbr;
+  int64_t NK;
+  float *bh0n;
+};
+
+__global__ void k_fused_prologue(const PrologueItem *items) {
+  const PrologueItem it = items[blockIdx.y];
+  const int64_t n = max(it.df_n, max(it.N, it.NK));
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    if (x < it.df_n) it.df[x] = 0;
+    if (x < it.N) it.bh0[x] = it.bh[x];
+    if (x < it.NK) it.bh0n[x] = it.bh[it.nbr[x]];
+  }
+}
+
+struct FusedEpochs {
+  Handle *h0 = nullptr;
+  int fpl = 1, kpl = 1, ng = 1, n = 0, epochs = 0, ctas = 0;
+  size_t smem = 0;
+  int64_t maxlen = 1;
+  SgdArgs *d_args = nullptr;      // [epochs][n]
+  int32_t *d_cta = nullptr;       // [ctas]: instance of each CTA
+  PrologueItem *d_pro = nullptr;  // [n]
+};
+
+void fused_free(FusedEpochs *f) {
+  if (!f) return;
+  cudaFree(f->d_args);
+  cudaFree(f->d_cta);
+  cudaFree(f->d_pro);
+  delete f;
+}
+
+template <int FPL, int KPL>
+static lshmf_status fused_tile(FusedEpochs *f, Handle *const *hs, std::vector<SgdArgs> &args) {
+  Handle *h0 = hs[0];
+  const size_t cap = size_t(h0->smem_optin) - ((sizeof(SgdArgs) + 255) & ~size_t(255));
+  int ng = MAX_GROUPS;
+  for (int x = 0; x < f->n; ++x) {
+    int g = 1, sl = 1;
+    LSHMF_TRY((sgd_tile<FPL, KPL>(hs[x], args[x].maxu, cap, &g, &sl)));
+    ng = std::min(ng, g);
+  }
+  size_t smem = 0;
+  for (int x = 0; x < f->n; ++x) {
+    Handle *h = hs[x];
+    int ns = h->sgd_slots > 0 ? std::min(h->sgd_slots, MAX_SLOTS) : SGD_DEFAULT_SLOTS;
+    while (ns > 1 && sgd_smem<FPL, KPL>(ng, ns, args[x].maxu) > cap) --ns;
+    for (int e = 0; e < f->epochs; ++e) args[size_t(e) * f->n + x].nslots = ns;
+    smem = std::max(smem, sgd_smem<FPL, KPL>(ng, ns, args[x].maxu));
+  }
+  f->ng = ng;
+  f->smem = smem;
+  LSHMF_CUDA(h0, cudaFuncSetAttribute(k_sgd_fused<FPL, KPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  return LSHMF_OK;
+}
+
+lshmf_status fused_setup(Handle *const *hs, const lshmf_params *params, int32_t n, int32_t epoch0, int32_t epochs,
+                         FusedEpochs **out) {
+  *out = nullptr;
+  Handle *h0 = hs[0];
+  FusedEpochs *f = new FusedEpochs();
+  f->h0 = h0;
+  f->n = n;
+  f->epochs = epochs;
+  f->fpl = (h0->cfg.F + 31) / 32;
+  f->kpl = (h0->cfg.K + 31) / 32;
+  std::vector<SgdArgs> args(size_t(epochs) * n);
+  std::vector<PrologueItem> pro(n);
+  std::vector<std::pair<int64_t, int32_t>> by_size;
+  lshmf_status s = LSHMF_OK;
+  for (int32_t x = 0; x < n && s == LSHMF_OK; ++x) {
+    Handle *h = hs[x];
+    const lshmf_config &c = h->cfg;
+    if ((c.F + 31) / 32 != f->fpl || (c.K + 31) / 32 != f->kpl || h->device != h0->device) {
+      s = set_err(h0, LSHMF_EINVAL, "batch: fused instances need the same ceil(F/32), ceil(K/32) and device");
+      break;
+    }
+    for (int32_t e = 0; e < epochs && s == LSHMF_OK; ++e) s = sgd_args(h, &params[x], epoch0 + e, false, args[size_t(e) * n + x]);
+    if (s != LSHMF_OK) {
+      if (h != h0) set_err(h0, s, "batch: instance %d: %s", x, h->last_error.c_str());
+      break;
+    }
+    TrainLayout &tl = h->tl;
+    pro[x] = PrologueItem{tl.df.as<int32_t>(), int64_t(sgd_flags_bytes(c.P) / 4), params[x].bh, tl.bh0.as<float>(),
+                          c.N, tl.nbr.as<int32_t>(), c.N * c.K, tl.bh0n.as<float>()};
+    f->maxlen = std::max(f->maxlen, std::max(pro[x].df_n, std::max(pro[x].N, pro[x].NK)));
+    by_size.push_back({tl.nnz, x});
+  }
+  if (s == LSHMF_OK) {
+    if (f->fpl <= 1) s = f->kpl <= 1 ? fused_tile<1, 1>(f, hs, args) : fused_tile<1, 2>(f, hs, args);
+    else if (f->fpl <= 2) s = f->kpl <= 1 ? fused_tile<2, 1>(f, hs, args) : fused_tile<2, 2>(f, hs, args);
+    else if (f->fpl <= 4) s = f->kpl <= 1 ? fused_tile<4, 1>(f, hs, args) : fused_tile<4, 2>(f, hs, args);
+    else s = f->kpl <= 1 ? fused_tile<8, 1>(f, hs, args) : fused_tile<8, 2>(f, hs, args);
+  }
+  if (s != LSHMF_OK) {
+    fused_free(f);
+    return s;
+  }
+  // CTAs, largest instances first (CTAs start roughly in index order): min(P, SMs) per instance
+  std::stable_sort(by_size.begin(), by_size.end(), [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
+    return a.first > b.first;
+  });
+  std::vector<int32_t> cta;
+  for (const auto &bx : by_size) {
+    const int k = std::min(hs[bx.second]->num_sms, hs[bx.second]->cfg.P);
+    for (int q = 0; q < k; ++q) cta.push_back(bx.second);
+  }
+  f->ctas = int(cta.size());
+  cudaError_t e = cudaMalloc(&f->d_args, sizeof(SgdArgs) * args.size());
+  if (e == cudaSuccess) e = cudaMalloc(&f->d_cta, sizeof(int32_t) * cta.size());
+  if (e == cudaSuccess) e = cudaMalloc(&f->d_pro, sizeof(PrologueItem) * pro.size());
+  if (e == cudaSuccess) e = cudaMemcpy(f->d_args, args.data(), sizeof(SgdArgs) * args.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f->d_cta, cta.data(), sizeof(int32_t) * cta.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f->d_pro, pro.data(), sizeof(PrologueItem) * pro.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_err(h0, LSHMF_ENOMEM, "batch: fused setup: %s", cudaGetErrorString(e));
+    fused_free(f);
+    return LSHMF_ENOMEM;
+  }
+  *out = f;
+  return LSHMF_OK;
+}
+
+template <int FPL, int KPL>
+static lshmf_status fused_kernel(FusedEpochs *f, int32_t e, cudaStream_t st) {
+  Handle *h = f->h0;
+  LSHMF_LAUNCH(h, (k_sgd_fused<FPL, KPL>), f->ctas, 32 * (f->ng * (GP + 1) + 1), f->smem, st,
+               f->d_args + size_t(e) * f->n, f->d_cta, f->ng);
+  return LSHMF_OK;
+}
+
+lshmf_status fused_launch(FusedEpochs *f, int32_t e, cudaStream_t st) {
+  Handle *h = f->h0;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(f->maxlen, 256), 64));
+  LSHMF_LAUNCH(h, k_fused_prologue, dim3(gx, unsigned(f->n)), 256, 0, st, f->d_pro);
+  if (f->fpl <= 1) return f->kpl <= 1 ? fused_kernel<1, 1>(f, e, st) : fused_kernel<1, 2>(f, e, st);
+  if (f->fpl <= 2) return f->kpl <= 1 ? fused_kernel<2, 1>(f, e, st) : fused_kernel<2, 2>(f, e, st);
+  if (f->fpl <= 4) return f->kpl <= 1 ? fused_kernel<4, 1>(f, e, st) : fused_kernel<4, 2>(f, e, st);
+  return f->kpl <= 1 ? fused_kernel<8, 1>(f, e, st) : fused_kernel<8, 2>(f, e, st);
 }
 
 }  // namespace lshmf

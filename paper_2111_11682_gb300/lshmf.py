@@ -23,7 +23,7 @@ SYMBOLS = ["lshmf_create", "lshmf_destroy", "lshmf_last_error", "lshmf_check", "
            "lshmf_train_strata", "lshmf_training_stats", "lshmf_predict", "lshmf_rmse",
            "lshmf_ingest", "lshmf_topn", "lshmf_topn_async", "lshmf_topn_work_bytes", "lshmf_copy_serving",
            "lshmf_rmse_noalloc", "lshmf_build_neighbours_variant",
-           "lshmf_batch_create", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
+           "lshmf_batch_create", "lshmf_batch_create_fused", "lshmf_batch_plan", "lshmf_batch_run", "lshmf_batch_check", "lshmf_batch_kernels", "lshmf_batch_destroy"]
 
 GEN_RAND, GEN_RPCOS, GEN_MINHASH = 1, 2, 3
 OPT_MEMORY_LIMIT, OPT_WAIT_POLLS, OPT_SGD_SLOTS, OPT_TEST_WITHHOLD, OPT_SGD_GROUPS = 1, 2, 3, 4, 5
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "lshmf_topn_work_bytes": ([P, I64, I32], I64),
         "lshmf_copy_serving": ([P, P, P], ctypes.c_int),
         "lshmf_batch_create": ([P, CP, P, I32, I32, I32, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "lshmf_batch_create_fused": ([P, CP, I32, I32, I32, ctypes.POINTER(P)], ctypes.c_int),
         "lshmf_batch_plan": ([P, I32, I32, P, P], ctypes.c_int),
         "lshmf_batch_run": ([P, P], ctypes.c_int),
         "lshmf_batch_check": ([P, P], ctypes.c_int),
@@ -344,10 +345,12 @@ class Batch:
     """lshmf_batch_*: epochs [epoch0, epoch0 + epochs) of every (model, params) pair recorded as one
     CUDA graph, instances over `branches` parallel branches (round-robin, or longest-first by `cost`).
     Branches run concurrently on at most CUDA_DEVICE_MAX_CONNECTIONS hardware queues (default 8,
-    at most 32; the variable is read when CUDA initialises, so set it before the first CUDA call).  Keeps references to the
-    models and parameter tensors (they must stay alive and unchanged in shape while the batch lives)."""
+    at most 32; the variable is read when CUDA initialises, so set it before the first CUDA call).
+    fused=True (lshmf_batch_create_fused): one launch of the epoch kernel per epoch for all instances
+    instead of branches (branches and cost are then unused).  Keeps references to the models and
+    parameter tensors (they must stay alive and unchanged in shape while the batch lives)."""
 
-    def __init__(self, models, params, epoch0=0, epochs=1, branches=1, cost=None):
+    def __init__(self, models, params, epoch0=0, epochs=1, branches=1, cost=None, fused=False):
         if len(models) != len(params) or not models or (cost is not None and len(cost) != len(models)):
             raise ValueError("Batch: need one Params (and one cost, if given) per model")
         self.lib = load()
@@ -356,10 +359,13 @@ class Batch:
         self._cp = (_CParams * len(params))(*(p._c() for p in params))
         cst = (ctypes.c_double * len(cost))(*map(float, cost)) if cost is not None else None
         b = ctypes.c_void_p()
-        st = self.lib.lshmf_batch_create(hs, self._cp, cst, len(models), epoch0, epochs, branches, ctypes.byref(b))
+        if fused:
+            st = self.lib.lshmf_batch_create_fused(hs, self._cp, len(models), epoch0, epochs, ctypes.byref(b))
+        else:
+            st = self.lib.lshmf_batch_create(hs, self._cp, cst, len(models), epoch0, epochs, branches, ctypes.byref(b))
         if st != OK:
             msgs = "; ".join(m.lib.lshmf_last_error(m.h).decode() for m in models if m.lib.lshmf_last_error(m.h))
-            raise LshmfError(st, "lshmf_batch_create failed" + (f" ({msgs})" if msgs else ""))
+            raise LshmfError(st, "lshmf_batch_create%s failed" % ("_fused" if fused else "") + (f" ({msgs})" if msgs else ""))
         self.b = b
 
     @property

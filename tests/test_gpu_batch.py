@@ -71,6 +71,47 @@ def test_batch_equals_separate_calls(instances, branches, with_cost):
     b.close()
 
 
+def test_fused_batch_equals_separate_calls(instances):
+    """One launch of the epoch kernel per epoch for all instances (lshmf_batch_create_fused): bit-identical
+    to separate lshmf_train_epoch calls, over two replays; 2 kernels per epoch for the whole batch."""
+    E0, E = 1, 2
+    alone = []
+    for _, _, m, p, _ in instances:
+        q = p.clone()
+        for e in range(E0, E0 + E):
+            m.train_epoch(q, e)
+        alone.append(q)
+    torch.cuda.synchronize()
+    ps = [p.clone() for _, _, _, p, _ in instances]
+    b = Batch([m for _, _, m, _, _ in instances], ps, epoch0=E0, epochs=E, fused=True)
+    assert b.kernels == 2 * E
+    for rep in range(2):
+        if rep == 1:
+            for q, (_, _, m, _, _) in zip(alone, instances):
+                for e in range(E0, E0 + E):
+                    m.train_epoch(q, e)
+        b.run()
+        b.check()
+        for x, (q, g) in enumerate(zip(alone, ps)):
+            for name in ("U", "V", "b", "bh", "W", "C"):
+                assert torch.equal(getattr(q, name), getattr(g, name)), (rep, x, name)
+    b.close()
+
+
+def test_fused_batch_rejects_mixed_kernel_shapes(instances):
+    """Instances whose F needs another instantiation of the epoch kernel cannot share a launch."""
+    w, _, m, p, data = instances[0]
+    w2 = replace(w, name="wide", F=64)
+    d2 = synth.generate(w2)
+    m2 = LshMF(config_from_workload(w2))
+    p2 = Params.from_init(d2["U0"], d2["V0"], w2.K, "cuda:0")
+    p2.mu = m2.prepare_training(*data)
+    with pytest.raises(LshmfError) as e:
+        Batch([m, m2], [p.clone(), p2], epochs=1, fused=True)
+    assert e.value.status == lshmf.EINVAL
+    m2.close()
+
+
 def test_batch_rejects_bad_lists(instances):
     ms = [m for _, _, m, _, _ in instances]
     ps = [p for _, _, _, p, _ in instances]
@@ -103,9 +144,11 @@ def test_autotune_returns_a_prepared_model(instances):
 C5_SHAPES = [(1000, 500, 10_000, 4, 1, 0), (2500, 900, 40_000, 8, 2, 2), (4000, 1500, 90_000, 16, 3, 1)]
 
 
-def test_c5_shaped_batch_matches_the_oracle():
+@pytest.mark.parametrize("fused", [False, True])
+def test_c5_shaped_batch_matches_the_oracle(fused):
     """Instances of the batched workload's shape (F = 32, K = 16, simLSH neighbours from L = 8 tables of
-    8 bits, beta = 0.3) at different P and SGD tiles, trained two epochs in one graph on two branches;
+    8 bits, beta = 0.3) at different P and SGD tiles, trained two epochs in one graph (on two branches,
+    or fused: one launch of the epoch kernel per epoch for all three);
     each against the FP64 oracle: neighbours bit-exact, per group max |gpu - oracle| <= 1e-4 max
     |oracle| after both epochs."""
     import os
@@ -132,7 +175,7 @@ def test_c5_shaped_batch_matches_the_oracle():
         p = Params.from_init(d["U0"], d["V0"], w.K, "cuda:0")
         p.mu = mu
         runs.append((w, d, m, p, onbr, mu))
-    b = Batch([r[2] for r in runs], [r[3] for r in runs], epoch0=0, epochs=E, branches=2)
+    b = Batch([r[2] for r in runs], [r[3] for r in runs], epoch0=0, epochs=E, branches=2, fused=fused)
     b.run()
     b.check()
     prev = oracle.set_threads(os.cpu_count() or 1)
