@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_2111_11682_gb300 import serve
-from paper_2111_11682_gb300.serve import Server, latency_summary, poisson_times
+from paper_2111_11682_gb300.serve import Server, latency_summary, poisson_times, split_summary
 
 
 class FakeModel:
@@ -205,3 +205,17 @@ def test_bad_query_fails_alone_and_errors_do_not_stop_the_loop(plenty):
     after = s.submit_topn(np.array([5]))
     s.drain()
     assert "rejected" in u.error and after.error is None and m.cfg.M == 50 and s.cur == 0
+
+
+def test_split_summary_separates_queue_wait_from_the_call():
+    reqs = []
+    for k in range(100):
+        q = serve.Request("topn", (np.array([0]),))
+        q.arrival, q.issued, q.done = 0.0, (k + 1) / 1000.0, (k + 1) / 1000.0 + 0.002
+        reqs.append(q)
+    never = serve.Request("topn", (np.array([0]),))        # refused before any call: not counted
+    never.error = "not enough free device memory"
+    s = split_summary(reqs + [never])
+    assert s["wait_p50_ms"] == pytest.approx(50.5) and s["call_p50_ms"] == pytest.approx(2.0)
+    assert s["call_p99_ms"] == pytest.approx(2.0) and s["wait_p99_ms"] == pytest.approx(99.01)
+    assert split_summary([never]) == {}
