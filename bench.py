@@ -661,7 +661,7 @@ def sgd_roofline(stats, w, epoch_ms, P):
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": prof.get("dram_bytes_per_epoch") if prof else None,
             "traffic_per_launch": prof.get("dram_bytes_per_launch") if prof else None,
-            "traffic_note": "ncu DRAM bytes per epoch (P launches), like achieved; from profiles/dram_traffic.json",
+            "traffic_note": "ncu DRAM bytes per epoch (one launch), like achieved; from profiles/dram_traffic.json",
             "algorithmic_bytes_per_epoch": int(bytes_ep),
             "min_bytes_per_epoch": int(sgd_min_bytes_per_epoch(stats, w)),
             "min_bytes_achieved_gbs": round(sgd_min_bytes_per_epoch(stats, w) / (ep_med / 1e3) / 1e9, 1),
