@@ -6,7 +6,9 @@ A step is one whole training job on the Netflix-shaped workload
 training layout with the explicit-neighbour index, 10 stratified SGD epochs,
 held-out RMSE.  `value` = rating-updates/s = epochs * nnz_train / step time,
 inputs resident in HBM.  `e2e` = the same with the inputs copied from pinned
-host memory inside every timed step and the RMSE read back.
+host memory inside every timed step and the RMSE read back.  P and the SGD
+kernel's tile are autotuned, untimed, before the timed steps unless --P is
+given.
 
 --impl reference times the FP64 CPU oracle (the only reference there is: the
 paper ships no code) on a bounded sample of the same workload.
